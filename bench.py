@@ -1,0 +1,538 @@
+"""Benchmark of the batched Lorenz-cipher path (one JSON line on stdout).
+
+Workload (default): 4096 messages with log-uniform sizes in [1 KiB, 4 MiB]
+(seeded), each with its own 8-32-char password; messages 0..2047 are
+encrypted, 2048..4095 decrypted (their inputs are ciphertexts of seeded
+plaintexts, made before timing).  One step = one lc_run_batch: host key
+schedules (cached), the flattened part table, the persistent cipher kernel
+and the verdict/finalize kernel, replayed from a CUDA graph.
+
+  value   message bytes / second over K timed steps, inputs resident in HBM
+  e2e     the same through lc_run_batch_host: pinned host buffers in and out,
+          host<->device copies inside the timed region
+  roofline  the cipher kernel's FP64 operation rate against the FP64 issue
+          peak (the kernel is bound by binary64 arithmetic, not HBM)
+  per_message_launch  a sample of the same messages launched one per call
+  cpu_baseline  the CPU oracle on the host cores, on a bounded sample
+
+--impl reference times the CPU oracle (the only reference implementation
+of this method) on a bounded sample of the same workload.
+
+Multi-GPU (torchrun, N > 1): every rank runs its own copy of the workload
+(weak scaling, no data-path collective); timing is max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Bit-exact encrypt/decrypt GB/s, batched vs per-message launch; served p50/p99 ms"
+UNIT = "GB/s"
+WORKLOAD = ("batched: 4096 messages, log-uniform 1 KiB-4 MiB, per-message 8-32-char passwords, "
+            "half encrypt / half decrypt, parallel mode (4096-byte parts), one persistent launch "
+            "from a CUDA graph per step")
+NOMINAL_FP64_TFLOPS = 1.25  # recipe: GB300 dense FP64, counting a DFMA as 2 flops
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (CPU-testable with gloo)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return ws, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def workload_spec(count):
+    from paper_1201_3114_gb300 import synth
+    return synth.cfg4_spec(count=count)
+
+
+def fp64_ops_per_launch(sizes, n_warm=3000, steps=1, B=4096, T=8):
+    """Algorithmic binary64 operations (each DADD/DMUL one operation, no FMA)
+    of one launch over messages of these plaintext sizes, and the bytes each
+    trajectory handles: per part 15 n_warm (warm-up) + 4 (start point)
+    + 3 (first alpha scaling), per byte (body and tag) 15 S (Euler) + 1 (kick)
+    + 3 (alpha scaling) + 3 (r += a')."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    parts = np.maximum(1, -(-sizes // B))
+    traj_bytes = sizes + T * parts
+    per_part = 15 * n_warm + 4 + 3
+    per_byte = 15 * steps + 1 + 3 + 3
+    ops = int(parts.sum()) * per_part + int(traj_bytes.sum()) * per_byte
+    return ops, int(parts.sum()), int(traj_bytes.sum())
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1201_3114_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h", ".cpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM traffic per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "batch_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != source_hash():
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_plan(spec, target_bytes):
+    """(message, first part, parts) triples covering ~target_bytes, spread
+    over all messages in proportion to their size."""
+    sizes = spec["sizes"]
+    total = int(sizes.sum())
+    frac = min(1.0, target_bytes / max(1, total))
+    plan = []
+    for m, n in enumerate(sizes):
+        nb = max(1, -(-int(n) // 4096))
+        take = max(1, int(round(nb * frac)))
+        plan.append((m, 0, min(nb, take)))
+    return plan
+
+
+def run_oracle_sample(spec, plan, threads):
+    """Run the sampled parts through the oracle on `threads` host threads.
+    Returns (message bytes processed, wall seconds)."""
+    import oracle as O
+    from paper_1201_3114_gb300 import synth
+    prm = O.params()
+    jobs = []
+    for m, b0, nb in plan:
+        n = int(spec["sizes"][m])
+        key = O.key_schedule(spec["pws"][m], prm)
+        lo, hi = b0 * 4096, min(n, (b0 + nb) * 4096)
+        P = np.zeros(n, dtype=np.uint8)
+        P[lo:hi] = synth.uniform_bytes(spec["data_seeds"][m], hi - lo, lo)
+        Cb = np.zeros(O.ciphertext_len(n, O.PARALLEL, prm), dtype=np.uint8)
+        jobs.append((spec["dirs"][m], key, P, n, Cb, b0, b0 + nb, hi - lo))
+    done = []
+    lock = threading.Lock()
+    it = iter(jobs)
+
+    def worker():
+        while True:
+            with lock:
+                job = next(it, None)
+            if job is None:
+                return
+            d, key, P, n, Cb, b0, b1, nbytes = job
+            if d == 0:
+                O.encrypt_blocks(key, P, n, Cb, b0, b1, prm)
+            else:
+                O.decrypt_blocks(key, Cb, n, P, b0, b1, prm)
+            with lock:
+                done.append(nbytes)
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    return int(sum(done)), time.perf_counter() - t0
+
+
+def reference_arm(args):
+    """The CPU oracle timed on the host cores, on a bounded sample of the
+    workload per step (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    spec = workload_spec(args.messages)
+    threads = os.cpu_count() or 1
+    plan = oracle_sample_plan(spec, args.ref_sample_mb << 20)
+    for _ in range(args.warmup):
+        run_oracle_sample(spec, plan, threads)
+    tot_b, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        b, s = run_oracle_sample(spec, plan, threads)
+        tot_b += b
+        tot_s += s
+    v = tot_b / tot_s / 1e9
+    sample = "%d MiB of parts per step spread over all %d messages (first parts of each)" % (
+        tot_b // args.steps >> 20, len(spec["sizes"]))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "messages": len(spec["sizes"]), "mode": "parallel",
+                   "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def profile_case(args):
+    """One message of args.profile_case MiB, parallel-mode encryption per step."""
+    import torch
+    from paper_1201_3114_gb300 import lc
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.profile_case << 20
+    ctx = lc.Context(0)
+    P = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lc.check(lc.lc_synth_uniform(P, n, 0x1201311400CA5E, 0, stream))
+    Cb = torch.empty(ctx.ciphertext_len(n), dtype=torch.uint8, device="cuda")
+    pw = b"profile-case-24-chars-pw"
+    for _ in range(args.warmup):
+        lc.check(lc.lc_encrypt(ctx.handle, pw, P, n, Cb, Cb.numel(), lc.LC_PARALLEL, stream))
+    lc.check(lc.lc_ctx_timing(ctx.handle, True))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lc.check(lc.lc_encrypt(ctx.handle, pw, P, n, Cb, Cb.numel(), lc.LC_PARALLEL, stream))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kms, kn = lc.lc_ctx_kernel_time(ctx.handle)
+    ops, parts, _ = fp64_ops_per_launch([n])
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": "profile", "mib": args.profile_case, "ms_per_step": ms,
+                      "GBps": n / ms / 1e6, "kernel_ms": kms / max(1, kn),
+                      "fp64_gops": ops / (kms / max(1, kn)) / 1e6, "source_hash": source_hash()}))
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--messages", type=int, default=4096)
+    ap.add_argument("--per-message-sample", type=int, default=256)
+    ap.add_argument("--cpu-sample-mb", type=int, default=96)
+    ap.add_argument("--ref-sample-mb", type=int, default=96)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="MIB",
+                    help="only time one MIB-MiB parallel-mode encryption per step (a small "
+                         "case for ncu captures); prints a short JSON line")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.profile_case:
+        return profile_case(args)
+
+    import torch
+    from paper_1201_3114_gb300 import lc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist("nccl" if ws > 1 else "gloo")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    spec = workload_spec(args.messages)
+    sizes, pws, seeds, dirs = spec["sizes"], spec["pws"], spec["data_seeds"], spec["dirs"]
+    count = len(sizes)
+    ctx = lc.Context(local)
+    if args.tune:
+        lc.lc_tune(ctx.handle, 0, stream)
+    launch = lc.lc_ctx_get_launch(ctx.handle)
+
+    # ---- device arenas: plaintexts, ciphertexts (decrypt inputs), outputs
+    def aligned(v):
+        return (v + 255) & ~255
+
+    p_off, c_off, o_off = [], [], []
+    ptot = ctot = otot = 0
+    clen = [ctx.ciphertext_len(int(n)) for n in sizes]
+    for m in range(count):
+        p_off.append(ptot)
+        ptot = aligned(ptot + int(sizes[m]))
+        c_off.append(ctot)
+        ctot = aligned(ctot + (clen[m] if dirs[m] == 1 else 0))
+        o_off.append(otot)
+        otot = aligned(otot + (clen[m] if dirs[m] == 0 else int(sizes[m])))
+    Parena = torch.empty(ptot, dtype=torch.uint8, device=dev)
+    Carena = torch.empty(max(ctot, 256), dtype=torch.uint8, device=dev)
+    Oarena = torch.empty(otot, dtype=torch.uint8, device=dev)
+    for m in range(count):
+        lc.check(lc.lc_synth_uniform(Parena.data_ptr() + p_off[m], int(sizes[m]), seeds[m], 0, stream))
+    enc_items = [(pws[m], 0, Parena.data_ptr() + p_off[m], int(sizes[m]),
+                  Carena.data_ptr() + c_off[m], clen[m]) for m in range(count) if dirs[m] == 1]
+    st_setup = torch.zeros(max(1, len(enc_items)), dtype=torch.int32, device=dev)
+    lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(enc_items), st_setup, lc.LC_PARALLEL, stream))
+    items = []
+    for m in range(count):
+        if dirs[m] == 0:
+            items.append((pws[m], 0, Parena.data_ptr() + p_off[m], int(sizes[m]),
+                          Oarena.data_ptr() + o_off[m], clen[m]))
+        else:
+            items.append((pws[m], 1, Carena.data_ptr() + c_off[m], clen[m],
+                          Oarena.data_ptr() + o_off[m], int(sizes[m])))
+    batch = lc.Batch(items)
+    status = torch.zeros(count, dtype=torch.int32, device=dev)
+    msg_bytes = int(sizes.sum())
+
+    # ---- warm-up (also checks every verdict)
+    for _ in range(args.warmup):
+        lc.check(lc.lc_run_batch(ctx.handle, batch, status, lc.LC_PARALLEL, stream))
+    torch.cuda.synchronize()
+    bad = int((status != 0).sum())
+    if bad:
+        raise SystemExit("warm-up: %d requests failed" % bad)
+    dec_ok = all(torch.equal(Oarena[o_off[m]:o_off[m] + int(sizes[m])],
+                             Parena[p_off[m]:p_off[m] + int(sizes[m])])
+                 for m in range(count) if dirs[m] == 1)
+    if not dec_ok:
+        raise SystemExit("warm-up: a decryption did not reproduce its plaintext")
+
+    # ---- timed region (device-resident inputs)
+    lc.check(lc.lc_ctx_timing(ctx.handle, True))
+    launches0 = lc.lc_ctx_launch_count(ctx.handle)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lc.check(lc.lc_run_batch(ctx.handle, batch, status, lc.LC_PARALLEL, stream))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    gpu_launches = lc.lc_ctx_launch_count(ctx.handle) - launches0
+    kern_ms, kern_n = lc.lc_ctx_kernel_time(ctx.handle)
+    lc.check(lc.lc_ctx_timing(ctx.handle, False))
+    elapsed_ms = max_over_ranks(elapsed_ms, dev if ws > 1 else None)
+    value = ws * msg_bytes * args.steps / (elapsed_ms * 1e-3) / 1e9
+    ms_per_step = elapsed_ms / args.steps
+
+    # ---- roofline of the cipher kernel
+    prm = lc.lc_ctx_get_params(ctx.handle)
+    ops, parts, traj_bytes = fp64_ops_per_launch(sizes, prm.n_warm, prm.steps_per_byte,
+                                                  prm.block_len, prm.tag_len)
+    kern_avg_ms = kern_ms / max(1, kern_n)
+    achieved = ops / (kern_avg_ms * 1e-3) / 1e9  # G FP64 ops / s
+    pipes = lc.lc_probe_pipes(local)
+    peak = NOMINAL_FP64_TFLOPS * 1e3 / 2.0
+    traffic = committed_traffic()
+    roofline = {
+        "bound": "alu", "unit": "G FP64 op/s", "achieved": achieved, "peak": peak,
+        "frac": achieved / peak,
+        "peak_source": "recipe nominal 1.25 TFLOP/s FP64 / 2 flops per DFMA slot",
+        "peak_probe": pipes.dadd_gops, "frac_of_probe": achieved / pipes.dadd_gops,
+        "ops_per_launch": ops, "kernel_ms": kern_avg_ms, "kernel": "batch_kernel",
+        "traffic": traffic["bytes_per_launch"] if traffic else None,
+        "hbm_bytes_algorithmic": 2 * msg_bytes + 8 * parts,
+    }
+
+    # ---- per-message launches (same messages, one request per call)
+    pm = None
+    if args.per_message_sample and rank == 0:
+        rng = np.random.default_rng(7)
+        order = np.argsort(sizes)
+        pick = order[np.linspace(0, count - 1, min(count, args.per_message_sample)).astype(int)]
+        s1 = torch.zeros(1, dtype=torch.int32, device=dev)
+        singles = [lc.Batch([items[m]]) for m in pick]
+        for b in singles[:8]:
+            lc.lc_run_batch(ctx.handle, b, s1, lc.LC_PARALLEL, stream)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for b in singles:
+            lc.check(lc.lc_run_batch(ctx.handle, b, s1, lc.LC_PARALLEL, stream))
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pm_bytes = int(sizes[pick].sum())
+        pm_ms = a0.elapsed_time(a1)
+        pm_val = pm_bytes / (pm_ms * 1e-3) / 1e9
+        pm = {"value": pm_val, "unit": UNIT, "messages": len(pick),
+              "sample": "size-stratified messages of the same workload, one lc_run_batch each",
+              "batched_over_per_message": value / ws / pm_val}
+        del rng
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hin_tot = sum(it[3] for it in items)
+        hout_tot = sum(it[5] for it in items)
+        hin = torch.empty(hin_tot, dtype=torch.uint8).pin_memory()
+        hout = torch.empty(hout_tot, dtype=torch.uint8).pin_memory()
+        hitems, a, b_ = [], 0, 0
+        for m, it in enumerate(items):
+            src = Parena if it[1] == 0 else Carena
+            off = (p_off[m] if it[1] == 0 else c_off[m])
+            hin[a:a + it[3]].copy_(src[off:off + it[3]])
+            hitems.append((it[0], it[1], hin.data_ptr() + a, it[3], hout.data_ptr() + b_, it[5]))
+            a += it[3]
+            b_ += it[5]
+        hbatch = lc.Batch(hitems)
+        hstat = np.zeros(count, dtype=np.int32)
+        for _ in range(2):
+            lc.check(lc.lc_run_batch_host(ctx.handle, hbatch, hstat, lc.LC_PARALLEL, stream))
+        assert (hstat == 0).all()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            lc.check(lc.lc_run_batch_host(ctx.handle, hbatch, hstat, lc.LC_PARALLEL, stream))
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dev if ws > 1 else None)
+        e2e = {"value": ws * msg_bytes * args.steps / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": hin_tot, "d2h_bytes_per_step": hout_tot + 4 * count,
+               "call": "lc_run_batch_host"}
+        del hin, hout
+
+    # ---- CPU oracle baseline
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_sample_mb:
+        threads = os.cpu_count() or 1
+        plan = oracle_sample_plan(spec, args.cpu_sample_mb << 20)
+        b_cpu, s_cpu = run_oracle_sample(spec, plan, threads)
+        cpu = {"value": b_cpu / s_cpu / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%.0f MiB: the first parts of every message in proportion to its size"
+                         % (b_cpu / 2 ** 20)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 messages and passwords)",
+            "config": {"workload": WORKLOAD, "messages": count, "message_bytes": msg_bytes,
+                       "parts": parts, "mode": "parallel",
+                       "l2": "inputs larger than L2 (%.2f GB per step)" % (msg_bytes / 1e9),
+                       "launch": {"threads_per_cta": launch.threads_per_cta,
+                                  "ctas_per_sm": launch.ctas_per_sm},
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "per_message_launch": pm, "clocks": clk,
+            "pipes_probe_gops": {k: round(v, 1) for k, v in pipes.as_dict().items()},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,239 @@
+/*
+ * lc.h -- C ABI of liblorenzcipher, a CUDA (sm_103a) implementation of the
+ * parallel Lorenz-attractor chaotic cipher of Marco, Martinez & Bruno,
+ * "Fast, parallel and secure cryptography algorithm using Lorenz's
+ * attractor" (arXiv 1201.3114).
+ *
+ * The problem statement is that of Sec. 1: a plaintext P of n_p bytes and a
+ * password pi give a ciphertext C = E_pi(P), and P = D_pi(C).  Sec. 2 adds
+ * that a changed ciphertext is detected (integrity); Sec. 5 splits the
+ * message into parts with their own initial conditions (parallel version).
+ *
+ * Conventions for every call below:
+ *   - Buffers named *_dev are device pointers (cudaMalloc / PyTorch CUDA
+ *     tensors) on the context's device; *_host are host pointers.  The caller
+ *     owns every buffer it passes; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls documented as "asynchronous"
+ *     return before the GPU has finished.
+ *   - Passwords are host bytes, 1..32 long (reading of the length limit of
+ *     Sec. 3.1); other lengths give LC_ERR_PASSWORD.
+ *   - Errors are returned as lc_status, never thrown.  There is no CPU
+ *     fallback: without a usable CUDA device every compute call returns
+ *     LC_ERR_CUDA.
+ *   - One lc_ctx must not be used by two host threads at once.
+ *   - In-place operation (input == output) is allowed: every byte is read by
+ *     the same thread before it is written.  Partly overlapping input and
+ *     output ranges give LC_ERR_ARG.
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LC_PARAMS_VERSION 1u
+
+typedef enum {
+  LC_OK = 0,
+  LC_ERR_ARG = 1,       /* null pointer, bad size, overlap, bad params */
+  LC_ERR_PASSWORD = 2,  /* password length outside 1..32 */
+  LC_ERR_LENGTH = 3,    /* ciphertext length no plaintext length maps to,
+                           or an output buffer that is too small */
+  LC_ERR_INTEGRITY = 4, /* decryption: a part's tag did not verify */
+  LC_ERR_CUDA = 5,      /* CUDA runtime error or no device */
+  LC_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  LC_ERR_NOMEM = 7      /* device workspace could not be allocated */
+} lc_status;
+
+typedef enum {
+  LC_PARALLEL = 0,  /* Sec. 5: independent parts of block_len bytes */
+  LC_SEQUENTIAL = 1 /* Sec. 3: one trajectory over the whole message */
+} lc_mode;
+
+typedef enum { LC_ENCRYPT = 0, LC_DECRYPT = 1 } lc_dir;
+
+/* Constants of the method.  Sec. 3.1 fixes sigma, rho, beta, bounds dt and
+ * lambda, gives n_it = 3000 and bounds k; the values left open are fixed by
+ * lc_params_default() (dt = 0.01, lambda = (1, 1, 20), k = (4, 4, 4),
+ * block_len = 4096, tag_len = 8, eta = 2^-24, one Euler step per byte,
+ * n_it read as the warm-up length).  Layout mirrors the oracle's. */
+typedef struct {
+  double sigma, rho, beta; /* Lorenz parameters, Sec. 3.1 */
+  double dt;               /* Euler step, Sec. 3.1 (0 < dt <= 0.027) */
+  uint32_t n_warm;         /* Euler steps before the first byte */
+  uint32_t steps_per_byte; /* applications of F per byte (1..4096) */
+  double lambda[3];        /* offset of r_0, Eq. 5 */
+  uint32_t k[3];           /* Omega_i in [0, k_i), Eq. 7; 1 <= k_i <= 8 */
+  uint32_t block_len;      /* bytes per part (Sec. 5), 16..2^24, multiple of 16 */
+  uint32_t tag_len;        /* integrity bytes per part, 1..8 */
+  double eta;              /* offset between consecutive parts' r_0 */
+} lc_params;
+
+typedef struct lc_ctx lc_ctx;
+
+/* LC_PARAMS_VERSION of the arithmetic this library implements. */
+uint32_t lc_version(void);
+
+/* Static English text for a status code (never NULL). */
+const char* lc_status_string(lc_status s);
+
+/* The default ("v1") constants described above. */
+lc_status lc_params_default(lc_params* out);
+
+/* Create a context on CUDA device `device`.  The context owns its device
+ * workspace (tables of parts and keys, verdict flags, the Theta table), a
+ * key cache and the captured CUDA graph of the batched path.  *out is NULL
+ * on failure.  Errors: LC_ERR_ARG (out NULL), LC_ERR_CUDA (no such device),
+ * LC_ERR_NOMEM. */
+lc_status lc_ctx_create(int device, lc_ctx** out);
+
+/* Wait for the context's work and release everything it owns. NULL is a no-op. */
+void lc_ctx_destroy(lc_ctx* ctx);
+
+/* Replace / read the constants used by later calls (default: v1).
+ * LC_ERR_ARG if a field is out of the documented range. */
+lc_status lc_ctx_set_params(lc_ctx* ctx, const lc_params* p);
+lc_status lc_ctx_get_params(const lc_ctx* ctx, lc_params* p);
+
+/* Ciphertext length for an n-byte message: n + tag_len * nblocks with
+ * nblocks = max(1, ceil(n / block_len)) in parallel mode, 1 in sequential
+ * mode (the empty message still carries one tag). */
+size_t lc_ciphertext_len(const lc_ctx* ctx, size_t n, lc_mode m);
+
+/* Inverse of lc_ciphertext_len; LC_ERR_LENGTH if no n maps to c_len. */
+lc_status lc_plaintext_len(const lc_ctx* ctx, size_t c_len, lc_mode m, size_t* n);
+
+/* Sec. 3.2 Steps 1-3 over every part of P (Sec. 5), C = E_pi(P).
+ * P_dev: n bytes (may be NULL when n == 0).  C_dev: c_cap >=
+ * lc_ciphertext_len(n, m) bytes; bytes [0, n) hold the coded message at the
+ * plaintext's offsets and the tags follow.  Asynchronous on `stream`.
+ * Errors: LC_ERR_ARG, LC_ERR_PASSWORD, LC_ERR_LENGTH (c_cap too small),
+ * LC_ERR_CUDA, LC_ERR_NOMEM. */
+lc_status lc_encrypt(lc_ctx* ctx, const uint8_t* pw, size_t pw_len,
+                     const uint8_t* P_dev, size_t n, uint8_t* C_dev, size_t c_cap,
+                     lc_mode m, void* stream);
+
+/* P = D_pi(C) and the integrity verdict of Sec. 2.  C_dev holds c_len bytes;
+ * P_dev receives n bytes (p_cap >= n).  Synchronises `stream`.  Returns
+ * LC_ERR_INTEGRITY if any part's tag failed, and then P is all zeros
+ * (fail-closed).  Other errors as lc_encrypt, LC_ERR_LENGTH for a c_len no
+ * plaintext length maps to. */
+lc_status lc_decrypt(lc_ctx* ctx, const uint8_t* pw, size_t pw_len,
+                     const uint8_t* C_dev, size_t c_len, uint8_t* P_dev, size_t p_cap,
+                     lc_mode m, void* stream);
+
+/* One request of a batch.  dir = LC_ENCRYPT: `in` holds in_len plaintext
+ * bytes and `out` receives lc_ciphertext_len(in_len) bytes.  dir =
+ * LC_DECRYPT: `in` holds an in_len-byte ciphertext and `out` receives the
+ * plaintext.  out_cap is the capacity of `out`. */
+typedef struct {
+  const uint8_t* pw;
+  uint32_t pw_len;
+  uint32_t dir;
+  const uint8_t* in;
+  size_t in_len;
+  uint8_t* out;
+  size_t out_cap;
+} lc_req;
+
+/* Batched path: every part of every request runs in one persistent kernel
+ * over a flattened table of parts, replayed from a CUDA graph.  Requests are
+ * independent and may mix directions and passwords; `in`/`out` are device
+ * pointers.  status_dev (device, `count` int32) receives each request's
+ * lc_status: LC_OK, LC_ERR_INTEGRITY (its output then zeroed), or the host
+ * validation error of that request (LC_ERR_PASSWORD / LC_ERR_LENGTH /
+ * LC_ERR_ARG; nothing is computed for it).  Asynchronous on `stream`.  The
+ * call itself fails (LC_ERR_ARG) only for a NULL ctx/reqs/status_dev or an
+ * unusable stream, LC_ERR_NOMEM / LC_ERR_CUDA for workspace or launch
+ * failures.  The request array and the passwords may be reused as soon as
+ * the call returns; the device buffers must stay valid until the stream
+ * reaches this point. */
+lc_status lc_run_batch(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_dev,
+                       lc_mode m, void* stream);
+
+/* lc_run_batch with HOST buffers: `in` / `out` are host pointers (pinned
+ * memory gives the best copy rate) and status_host is host memory.  The
+ * library copies the inputs to its own device staging area, runs the batch
+ * and copies the outputs and statuses back; returns after the stream has
+ * synchronised.  The call's return value is LC_OK unless the call itself
+ * failed; per-request results are in status_host. */
+lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count,
+                            int32_t* status_host, lc_mode m, void* stream);
+
+/* Launch shape of the batched kernel: threads per CTA (32..1024, multiple of
+ * 32), resident CTAs per SM for the persistent grid (0 = as many as fit),
+ * and 1 to stage input through shared memory (0 = direct 16-byte loads).
+ * The shape never changes results. */
+typedef struct {
+  uint32_t threads_per_cta;
+  uint32_t ctas_per_sm;
+  uint32_t smem_staging;
+  uint32_t reserved;
+} lc_launch;
+
+lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out);
+lc_status lc_ctx_set_launch(lc_ctx* ctx, const lc_launch* l);
+
+/* Autotuner: times the candidate launch shapes on a synthetic batch of
+ * `probe_bytes` (0 = 64 MiB) on `stream`, keeps the fastest in the context
+ * and returns it in *best (may be NULL).  Never changes results. */
+lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best);
+
+/* Accumulated device time of the context's main cipher kernel since the
+ * last reset, measured with CUDA events on the launching stream (enabled by
+ * lc_ctx_timing(ctx, 1); reading synchronises those events). */
+lc_status lc_ctx_timing(lc_ctx* ctx, int enable);
+lc_status lc_ctx_kernel_time(lc_ctx* ctx, double* total_ms, uint64_t* launches);
+
+/* Number of kernels the library has launched through this context. */
+uint64_t lc_ctx_launch_count(const lc_ctx* ctx);
+
+/* Host-only inspection of the key schedule of Sec. 3.1 (Eqs. 2-7): a' = g(a),
+ * the initial mu and Omega for password pw under parameters p (NULL =
+ * defaults).  Needs no GPU.  LC_ERR_PASSWORD for a length outside 1..32,
+ * LC_ERR_ARG for a NULL out or invalid p. */
+typedef struct {
+  double aprime[3];
+  uint32_t mu[3];
+  uint32_t omega[3];
+  uint32_t L, D;
+} lc_key_info_t;
+lc_status lc_key_info(const lc_params* p, const uint8_t* pw, size_t pw_len, lc_key_info_t* out);
+
+/* Host-only validation of a batch, exactly as lc_run_batch performs it:
+ * init_status (host, `count` int32) receives LC_OK or the request's
+ * validation error, *nrows the number of trajectories (parts) the valid
+ * requests need.  Needs no GPU. */
+lc_status lc_plan_batch(const lc_params* p, const lc_req* reqs, size_t count, lc_mode m,
+                        int32_t* init_status, uint64_t* nrows);
+
+/* Measured issue rates (results per second / 1e9) of the SM pipes the cipher
+ * uses, from throughput microbenchmarks on `device` (not part of the paper's
+ * method; the roofline denominators of the FP64-bound kernel).  ialu counts
+ * 32-bit integer add/logic results, imad 32-bit integer multiply-adds, ffma
+ * fp32 fused multiply-adds.  Synchronises the device. */
+typedef struct {
+  double dadd_gops, dmul_gops, cvt_gops;
+  double imad_gops, ialu_gops, ffma_gops;
+  double sm_clock_mhz;
+  uint32_t sm_count, reserved;
+} lc_pipe_rates;
+lc_status lc_probe_pipes(int device, lc_pipe_rates* out);
+
+/* Seeded input generator (not part of the paper's method): writes bytes
+ * [offset, offset + n) of the counter-based SplitMix64 byte stream `seed`
+ * (Steele, Lea & Flood 2014; byte j = byte j mod 8, little-endian, of word
+ * j / 8, word i = mix(seed + (i + 1) * 0x9E3779B97F4A7C15)) to dst_dev.
+ * Asynchronous on `stream`. */
+lc_status lc_synth_uniform(uint8_t* dst_dev, size_t n, uint64_t seed, uint64_t offset,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -8,7 +8,7 @@
  * built with -O2 -ffp-contract=off so that every written operation is one
  * rounding.  Each function names the passage of the paper it restates.
  * Where the paper is silent, ambiguous or garbled, the reading taken is
- * stated next to the code (readings R1..R22 of the design notes).
+ * stated next to the code as a numbered reading (R1..R22).
  */
 #include "lco.h"
 

@@ -1,0 +1,840 @@
+// api.cu -- the C ABI of liblorenzcipher (include/lc.h): contexts, the
+// flattened part table of the batched path, its CUDA graph, host-buffer
+// staging, the launch-shape autotuner and kernel timing.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "keysched.h"
+#include "lc_internal.h"
+
+namespace lc {
+size_t batch_kernel_smem(bool k4);
+const void* batch_kernel_ptr(bool k4);
+cudaError_t launch_batch(bool k4, int grid, int block, const uint8_t* ws, uint32_t* scratch,
+                         const DevParams& p, const double* theta, cudaStream_t s);
+cudaError_t launch_finalize(int grid, const uint8_t* ws, const uint32_t* scratch, uint32_t block_len,
+                            cudaStream_t s);
+cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offset, cudaStream_t s);
+}  // namespace lc
+
+using namespace lc;
+
+namespace {
+
+constexpr int kFinalizeGrid = 1024;
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+struct Staging {
+  uint8_t* host = nullptr;  // pinned
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;  // the H2D copy out of this slot has finished
+  bool used = false;
+};
+
+}  // namespace
+
+struct lc_ctx {
+  int device = 0;
+  int sm_count = 0;
+  lc_params params{};
+  DevParams dparams{};
+  bool k4 = true;
+
+  double* theta_dev = nullptr;
+  uint8_t* ws_dev = nullptr;  // header | msgs | rows | init status
+  size_t ws_cap = 0;
+  uint32_t* scratch_dev = nullptr;  // counter(4 words) | fail flags
+  size_t fail_cap = 0;              // messages covered by the fail flags
+  int32_t* status_tmp_dev = nullptr;
+  size_t status_tmp_cap = 0;
+  uint8_t* io_dev = nullptr;  // staging for lc_run_batch_host
+  size_t io_cap = 0;
+
+  Staging staging[2];
+  int slot = 0;
+
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t ev_node_a = nullptr, ev_node_b = nullptr;
+  bool graph_valid = false;
+
+  lc_launch launch{256, 0, 0, 0};
+  int grid = 0;
+
+  std::unordered_map<std::string, HostKey> keys;
+
+  bool timing = false;
+  std::vector<EventPair> ev_free, ev_pending;
+  double total_ms = 0.0;
+  uint64_t timed_launches = 0;
+  uint64_t launches = 0;
+
+  std::vector<DevMsg> h_msgs;
+  std::vector<DevRow> h_rows;
+  std::vector<int32_t> h_init;
+};
+
+namespace {
+
+lc_status cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return LC_OK;
+  if (e == cudaErrorMemoryAllocation) return LC_ERR_NOMEM;
+  return LC_ERR_CUDA;
+}
+
+#define LC_CUDA(expr)                            \
+  do {                                           \
+    cudaError_t _e = (expr);                     \
+    if (_e != cudaSuccess) return cuda_fail(_e); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void to_dev_params(const lc_params& p, DevParams* d) {
+  d->sigma = p.sigma;
+  d->rho = p.rho;
+  d->beta = p.beta;
+  d->dt = p.dt;
+  d->eta = p.eta;
+  d->n_warm = p.n_warm;
+  d->steps_per_byte = p.steps_per_byte;
+  d->block_len = p.block_len;
+  d->tag_len = p.tag_len;
+  for (int i = 0; i < 3; i++) d->k[i] = p.k[i];
+  d->k_all4 = (p.k[0] == 4 && p.k[1] == 4 && p.k[2] == 4) ? 1u : 0u;
+}
+
+size_t nblocks_of(const lc_params& p, size_t n, lc_mode m) {
+  if (m == LC_SEQUENTIAL || n == 0) return 1;
+  return (n + p.block_len - 1) / p.block_len;
+}
+
+size_t ct_len(const lc_params& p, size_t n, lc_mode m) {
+  return n + (size_t)p.tag_len * nblocks_of(p, n, m);
+}
+
+bool pt_len(const lc_params& p, size_t c, lc_mode m, size_t* n) {
+  if (c < p.tag_len) return false;
+  if (m == LC_SEQUENTIAL) {
+    *n = c - p.tag_len;
+    return true;
+  }
+  const size_t per = (size_t)p.block_len + p.tag_len;
+  const size_t guess = c / per;
+  for (size_t nb = std::max<size_t>(guess, 1); nb <= guess + 1; nb++) {
+    if ((size_t)p.tag_len * nb > c) break;
+    const size_t cand = c - (size_t)p.tag_len * nb;
+    if (nblocks_of(p, cand, LC_PARALLEL) == nb) {
+      *n = cand;
+      return true;
+    }
+  }
+  return false;
+}
+
+bool ranges_conflict(const void* a, size_t alen, const void* b, size_t blen) {
+  if (a == b) return false;  // exact in-place is allowed
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return alen && blen && x < y + blen && y < x + alen;
+}
+
+lc_status get_key(lc_ctx* ctx, const uint8_t* pw, size_t n, const HostKey** out) {
+  if (pw == nullptr || n < 1 || n > 32) return LC_ERR_PASSWORD;
+  std::string k(reinterpret_cast<const char*>(pw), n);
+  auto it = ctx->keys.find(k);
+  if (it == ctx->keys.end()) {
+    HostKey hk;
+    lc_status st = key_schedule(ctx->params, pw, n, &hk);
+    if (st != LC_OK) return st;
+    if (ctx->keys.size() > 65536) ctx->keys.clear();
+    it = ctx->keys.emplace(std::move(k), hk).first;
+  }
+  *out = &it->second;
+  return LC_OK;
+}
+
+template <typename T>
+lc_status grow_device(T** ptr, size_t* cap, size_t need_elems, bool* changed) {
+  if (need_elems <= *cap) return LC_OK;
+  size_t n = std::max<size_t>(need_elems, *cap + *cap / 2);
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  LC_CUDA(cudaMalloc(reinterpret_cast<void**>(ptr), n * sizeof(T)));
+  *cap = n;
+  if (changed) *changed = true;
+  return LC_OK;
+}
+
+void release_graph(lc_ctx* ctx) {
+  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->exec = nullptr;
+  ctx->graph = nullptr;
+  ctx->ev_node_a = ctx->ev_node_b = nullptr;
+  ctx->graph_valid = false;
+}
+
+lc_status event_pair(lc_ctx* ctx, EventPair* ep) {
+  if (!ctx->ev_free.empty()) {
+    *ep = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+    return LC_OK;
+  }
+  LC_CUDA(cudaEventCreate(&ep->a));
+  LC_CUDA(cudaEventCreate(&ep->b));
+  return LC_OK;
+}
+
+lc_status drain_timing(lc_ctx* ctx) {
+  for (auto& ep : ctx->ev_pending) {
+    LC_CUDA(cudaEventSynchronize(ep.b));
+    float ms = 0.f;
+    LC_CUDA(cudaEventElapsedTime(&ms, ep.a, ep.b));
+    ctx->total_ms += ms;
+    ctx->timed_launches++;
+    ctx->ev_free.push_back(ep);
+  }
+  ctx->ev_pending.clear();
+  return LC_OK;
+}
+
+int resident_ctas(lc_ctx* ctx, int threads) {
+  int per_sm = 0;
+  const void* fn = batch_kernel_ptr(ctx->k4);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads,
+                                                    batch_kernel_smem(ctx->k4)) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm;
+}
+
+// Graph: clear the counter and fail flags -> event A -> persistent cipher
+// kernel -> event B -> finalize.  Kernel arguments are fixed workspace
+// pointers; the per-batch sizes live in the uploaded header, so replays
+// need no re-capture until the workspace moves or the shape changes.
+lc_status build_graph(lc_ctx* ctx) {
+  release_graph(ctx);
+  const int threads = (int)ctx->launch.threads_per_cta;
+  int per_sm = resident_ctas(ctx, threads);
+  if (ctx->launch.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)ctx->launch.ctas_per_sm);
+  ctx->grid = ctx->sm_count * per_sm;
+
+  EventPair ep;
+  lc_status st = event_pair(ctx, &ep);
+  if (st != LC_OK) return st;
+  ctx->ev_free.push_back(ep);
+
+  cudaStream_t s = ctx->cap_stream;
+  LC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(ctx->scratch_dev, 0, (4 + ctx->fail_cap) * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.a, s, cudaEventRecordExternal);
+  if (e == cudaSuccess)
+    e = launch_batch(ctx->k4, ctx->grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams,
+                     ctx->theta_dev, s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.b, s, cudaEventRecordExternal);
+  if (e == cudaSuccess)
+    e = launch_finalize(kFinalizeGrid, ctx->ws_dev, ctx->scratch_dev, ctx->params.block_len, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e != cudaSuccess ? e : e2);
+  }
+  ctx->graph = g;
+  size_t nn = 0;
+  LC_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  LC_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    LC_CUDA(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeEventRecord) {
+      cudaEvent_t ev;
+      LC_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+      if (ev == ep.a) ctx->ev_node_a = nd;
+      if (ev == ep.b) ctx->ev_node_b = nd;
+    }
+  }
+  LC_CUDA(cudaGraphInstantiate(&ctx->exec, g, 0));
+  ctx->graph_valid = true;
+  return LC_OK;
+}
+
+// Host validation of one request; LC_OK or the request's status code.
+int32_t validate_req(const lc_params& p, const lc_req& r, lc_mode m, size_t* n_out) {
+  size_t n = 0;
+  int32_t st = LC_OK;
+  if (r.dir > 1) {
+    st = LC_ERR_ARG;
+  } else if (r.dir == LC_ENCRYPT) {
+    n = r.in_len;
+    if ((n && !r.in) || !r.out) st = LC_ERR_ARG;
+    else if (r.out_cap < ct_len(p, n, m)) st = LC_ERR_LENGTH;
+    else if (ranges_conflict(r.in, n, r.out, ct_len(p, n, m))) st = LC_ERR_ARG;
+  } else {
+    if (!r.in) st = LC_ERR_ARG;
+    else if (!pt_len(p, r.in_len, m, &n)) st = LC_ERR_LENGTH;
+    else if (n && !r.out) st = LC_ERR_ARG;
+    else if (r.out_cap < n) st = LC_ERR_LENGTH;
+    else if (ranges_conflict(r.in, r.in_len, r.out, n)) st = LC_ERR_ARG;
+  }
+  if (st == LC_OK && (!r.pw || r.pw_len < 1 || r.pw_len > 32)) st = LC_ERR_PASSWORD;
+  *n_out = n;
+  return st;
+}
+
+
+// Validate the requests, build the message and part tables (parts sorted
+// longest first so warps hold parts of equal length), upload them and
+// replay the graph on `s`.
+lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_dev,
+                         lc_mode m, cudaStream_t s) {
+  const lc_params& p = ctx->params;
+  ctx->h_msgs.resize(count);
+  ctx->h_init.resize(count);
+  ctx->h_rows.clear();
+  size_t full_rows = 0;
+  std::vector<DevRow> partial;
+
+  for (size_t i = 0; i < count; i++) {
+    const lc_req& r = reqs[i];
+    DevMsg& M = ctx->h_msgs[i];
+    memset(&M, 0, sizeof M);
+    size_t n = 0;
+    const HostKey* key = nullptr;
+    int32_t init = validate_req(p, r, m, &n);
+    if (init == LC_OK) {
+      lc_status ks = get_key(ctx, r.pw, r.pw_len, &key);
+      if (ks != LC_OK) init = ks;
+    }
+    ctx->h_init[i] = init;
+    if (init != LC_OK) continue;
+    M.in = r.in;
+    M.out = r.out;
+    M.n = n;
+    for (int j = 0; j < 3; j++) {
+      M.base[j] = key->aprime[j] + p.lambda[j];  // one rounding, Eq. 5
+      M.aprime[j] = key->aprime[j];
+    }
+    M.key_bits = key->mu[0] | key->mu[1] << 2 | key->mu[2] << 4 | key->omega[0] << 8 |
+                 key->omega[1] << 12 | key->omega[2] << 16;
+    M.flags = (r.dir == LC_DECRYPT ? kFlagDecrypt : 0u) | (m == LC_SEQUENTIAL ? kFlagSequential : 0u);
+    const size_t nb = nblocks_of(p, n, m);
+    if (nb > 0xFFFFFFFFull) return LC_ERR_ARG;
+    for (size_t b = 0; b < nb; b++) {
+      const size_t len = (m == LC_SEQUENTIAL) ? n : std::min<size_t>(p.block_len, n - b * p.block_len);
+      DevRow row{(uint32_t)i, (uint32_t)b};
+      if (m == LC_PARALLEL && len == p.block_len) {
+        ctx->h_rows.push_back(row);
+        full_rows++;
+      } else {
+        partial.push_back(row);
+      }
+    }
+  }
+  // Longest first: full parts, then the rest by decreasing length.
+  auto row_len = [&](const DevRow& r) -> size_t {
+    const DevMsg& M = ctx->h_msgs[r.msg];
+    if (M.flags & kFlagSequential) return M.n;
+    return std::min<size_t>(p.block_len, M.n - (size_t)r.b * p.block_len);
+  };
+  std::stable_sort(partial.begin(), partial.end(),
+                   [&](const DevRow& a, const DevRow& b) { return row_len(a) > row_len(b); });
+  ctx->h_rows.insert(ctx->h_rows.end(), partial.begin(), partial.end());
+  if (ctx->h_rows.size() > 0xFFFFFFF0ull || count > 0xFFFFFFF0ull) return LC_ERR_ARG;
+
+  const size_t nrows = ctx->h_rows.size();
+  const size_t bytes = sizeof(DevHeader) + count * sizeof(DevMsg) + nrows * sizeof(DevRow) +
+                       count * sizeof(int32_t);
+
+  // Device workspace (graph is rebuilt whenever a buffer moves).
+  bool changed = !ctx->graph_valid;
+  lc_status st = grow_device(&ctx->ws_dev, &ctx->ws_cap, bytes, &changed);
+  if (st != LC_OK) return st;
+  size_t fail_need = std::max<size_t>(count, 1024);
+  if (fail_need > ctx->fail_cap) {
+    size_t cap_words = 4 + std::max(fail_need, ctx->fail_cap + ctx->fail_cap / 2);
+    if (ctx->scratch_dev) cudaFree(ctx->scratch_dev);
+    ctx->scratch_dev = nullptr;
+    ctx->fail_cap = 0;
+    LC_CUDA(cudaMalloc(&ctx->scratch_dev, cap_words * sizeof(uint32_t)));
+    LC_CUDA(cudaMemset(ctx->scratch_dev, 0, cap_words * sizeof(uint32_t)));
+    ctx->fail_cap = cap_words - 4;
+    changed = true;
+  }
+  if (changed) {
+    st = build_graph(ctx);
+    if (st != LC_OK) return st;
+  }
+
+  // Pinned staging, double-buffered: wait until the copy that last used
+  // this slot has left it.
+  Staging& sg = ctx->staging[ctx->slot];
+  ctx->slot ^= 1;
+  if (sg.used) LC_CUDA(cudaEventSynchronize(sg.done));
+  if (sg.cap < bytes) {
+    if (sg.host) cudaFreeHost(sg.host);
+    sg.host = nullptr;
+    sg.cap = 0;
+    size_t cap = std::max(bytes, (size_t)1 << 20);
+    LC_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&sg.host), cap, cudaHostAllocDefault));
+    sg.cap = cap;
+  }
+  if (!sg.done) LC_CUDA(cudaEventCreateWithFlags(&sg.done, cudaEventDisableTiming));
+  DevHeader hdr;
+  memset(&hdr, 0, sizeof hdr);
+  hdr.nrows = (uint32_t)nrows;
+  hdr.nmsgs = (uint32_t)count;
+  hdr.status_out = status_dev;
+  uint8_t* w = sg.host;
+  memcpy(w, &hdr, sizeof hdr);
+  w += sizeof hdr;
+  if (count) memcpy(w, ctx->h_msgs.data(), count * sizeof(DevMsg));
+  w += count * sizeof(DevMsg);
+  if (nrows) memcpy(w, ctx->h_rows.data(), nrows * sizeof(DevRow));
+  w += nrows * sizeof(DevRow);
+  if (count) memcpy(w, ctx->h_init.data(), count * sizeof(int32_t));
+
+  LC_CUDA(cudaMemcpyAsync(ctx->ws_dev, sg.host, bytes, cudaMemcpyHostToDevice, s));
+  LC_CUDA(cudaEventRecord(sg.done, s));
+  sg.used = true;
+
+  if (ctx->timing) {
+    EventPair ep;
+    st = event_pair(ctx, &ep);
+    if (st != LC_OK) return st;
+    LC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ctx->exec, ctx->ev_node_a, ep.a));
+    LC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ctx->exec, ctx->ev_node_b, ep.b));
+    ctx->ev_pending.push_back(ep);
+    if (ctx->ev_pending.size() > 4096) {
+      st = drain_timing(ctx);
+      if (st != LC_OK) return st;
+    }
+  }
+  LC_CUDA(cudaGraphLaunch(ctx->exec, s));
+  ctx->launches += 2;  // cipher kernel + finalize kernel
+  return LC_OK;
+}
+
+lc_status ensure_status_tmp(lc_ctx* ctx, size_t count) {
+  return grow_device(&ctx->status_tmp_dev, &ctx->status_tmp_cap, std::max<size_t>(count, 1), nullptr);
+}
+
+}  // namespace
+
+// ===========================================================================
+// Public ABI
+// ===========================================================================
+
+extern "C" {
+
+uint32_t lc_version(void) { return LC_PARAMS_VERSION; }
+
+const char* lc_status_string(lc_status s) {
+  switch (s) {
+    case LC_OK: return "ok";
+    case LC_ERR_ARG: return "invalid argument";
+    case LC_ERR_PASSWORD: return "password length outside 1..32 bytes";
+    case LC_ERR_LENGTH: return "invalid length or buffer too small";
+    case LC_ERR_INTEGRITY: return "integrity check failed";
+    case LC_ERR_CUDA: return "CUDA error";
+    case LC_ERR_TIMEOUT: return "device wait timed out";
+    case LC_ERR_NOMEM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+lc_status lc_params_default(lc_params* out) {
+  if (!out) return LC_ERR_ARG;
+  out->sigma = 10.0;
+  out->rho = 28.0;
+  out->beta = 8.0 / 3.0;
+  out->dt = 0.01;
+  out->n_warm = 3000;
+  out->steps_per_byte = 1;
+  out->lambda[0] = 1.0;
+  out->lambda[1] = 1.0;
+  out->lambda[2] = 20.0;
+  out->k[0] = out->k[1] = out->k[2] = 4;
+  out->block_len = 4096;
+  out->tag_len = 8;
+  out->eta = 1.0 / 16777216.0;
+  return LC_OK;
+}
+
+lc_status lc_ctx_create(int device, lc_ctx** out) {
+  if (!out) return LC_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LC_ERR_CUDA;
+  lc_ctx* ctx = new (std::nothrow) lc_ctx();
+  if (!ctx) return LC_ERR_NOMEM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  lc_params_default(&ctx->params);
+  to_dev_params(ctx->params, &ctx->dparams);
+  ctx->k4 = ctx->dparams.k_all4 != 0;
+  lc_status st = LC_OK;
+  cudaError_t e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->theta_dev, kThetaEntries * sizeof(double));
+  if (e == cudaSuccess) {
+    std::vector<double> th(kThetaEntries);
+    build_theta(th.data());
+    e = cudaMemcpy(ctx->theta_dev, th.data(), kThetaEntries * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    for (int k4 = 0; k4 < 2; k4++) {
+      e = cudaFuncSetAttribute(batch_kernel_ptr(k4 != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)batch_kernel_smem(k4 != 0));
+      if (e != cudaSuccess) break;
+    }
+  }
+  if (e != cudaSuccess) st = cuda_fail(e);
+  if (st != LC_OK) {
+    lc_ctx_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return LC_OK;
+}
+
+void lc_ctx_destroy(lc_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  release_graph(ctx);
+  for (auto& ep : ctx->ev_free) {
+    cudaEventDestroy(ep.a);
+    cudaEventDestroy(ep.b);
+  }
+  for (auto& ep : ctx->ev_pending) {
+    cudaEventDestroy(ep.a);
+    cudaEventDestroy(ep.b);
+  }
+  for (auto& sg : ctx->staging) {
+    if (sg.host) cudaFreeHost(sg.host);
+    if (sg.done) cudaEventDestroy(sg.done);
+  }
+  if (ctx->theta_dev) cudaFree(ctx->theta_dev);
+  if (ctx->ws_dev) cudaFree(ctx->ws_dev);
+  if (ctx->scratch_dev) cudaFree(ctx->scratch_dev);
+  if (ctx->status_tmp_dev) cudaFree(ctx->status_tmp_dev);
+  if (ctx->io_dev) cudaFree(ctx->io_dev);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}
+
+lc_status lc_ctx_set_params(lc_ctx* ctx, const lc_params* p) {
+  if (!ctx || !p || !params_valid(*p)) return LC_ERR_ARG;
+  ctx->params = *p;
+  to_dev_params(*p, &ctx->dparams);
+  ctx->k4 = ctx->dparams.k_all4 != 0;
+  ctx->keys.clear();
+  ctx->graph_valid = false;
+  return LC_OK;
+}
+
+lc_status lc_ctx_get_params(const lc_ctx* ctx, lc_params* p) {
+  if (!ctx || !p) return LC_ERR_ARG;
+  *p = ctx->params;
+  return LC_OK;
+}
+
+size_t lc_ciphertext_len(const lc_ctx* ctx, size_t n, lc_mode m) {
+  lc_params p;
+  if (ctx) p = ctx->params; else lc_params_default(&p);
+  return ct_len(p, n, m);
+}
+
+lc_status lc_plaintext_len(const lc_ctx* ctx, size_t c_len, lc_mode m, size_t* n) {
+  if (!n) return LC_ERR_ARG;
+  lc_params p;
+  if (ctx) p = ctx->params; else lc_params_default(&p);
+  return pt_len(p, c_len, m, n) ? LC_OK : LC_ERR_LENGTH;
+}
+
+lc_status lc_run_batch(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_dev, lc_mode m,
+                       void* stream) {
+  if (!ctx || (!reqs && count) || (!status_dev && count)) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  if (count == 0) return LC_OK;
+  DeviceGuard g(ctx->device);
+  return run_batch_impl(ctx, reqs, count, status_dev, m, static_cast<cudaStream_t>(stream));
+}
+
+lc_status lc_encrypt(lc_ctx* ctx, const uint8_t* pw, size_t pw_len, const uint8_t* P_dev, size_t n,
+                     uint8_t* C_dev, size_t c_cap, lc_mode m, void* stream) {
+  if (!ctx || (n && !P_dev) || !C_dev) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  if (pw_len < 1 || pw_len > 32 || !pw) return LC_ERR_PASSWORD;
+  if (c_cap < ct_len(ctx->params, n, m)) return LC_ERR_LENGTH;
+  if (ranges_conflict(P_dev, n, C_dev, ct_len(ctx->params, n, m))) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  lc_status st = ensure_status_tmp(ctx, 1);
+  if (st != LC_OK) return st;
+  lc_req r{pw, (uint32_t)pw_len, LC_ENCRYPT, P_dev, n, C_dev, c_cap};
+  return run_batch_impl(ctx, &r, 1, ctx->status_tmp_dev, m, static_cast<cudaStream_t>(stream));
+}
+
+lc_status lc_decrypt(lc_ctx* ctx, const uint8_t* pw, size_t pw_len, const uint8_t* C_dev, size_t c_len,
+                     uint8_t* P_dev, size_t p_cap, lc_mode m, void* stream) {
+  if (!ctx || !C_dev) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  size_t n = 0;
+  if (!pt_len(ctx->params, c_len, m, &n)) return LC_ERR_LENGTH;
+  if (n && !P_dev) return LC_ERR_ARG;
+  if (pw_len < 1 || pw_len > 32 || !pw) return LC_ERR_PASSWORD;
+  if (p_cap < n) return LC_ERR_LENGTH;
+  if (ranges_conflict(C_dev, c_len, P_dev, n)) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  lc_status st = ensure_status_tmp(ctx, 1);
+  if (st != LC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lc_req r{pw, (uint32_t)pw_len, LC_DECRYPT, C_dev, c_len, P_dev, p_cap};
+  st = run_batch_impl(ctx, &r, 1, ctx->status_tmp_dev, m, s);
+  if (st != LC_OK) return st;
+  int32_t verdict = LC_ERR_CUDA;
+  LC_CUDA(cudaMemcpyAsync(&verdict, ctx->status_tmp_dev, sizeof verdict, cudaMemcpyDeviceToHost, s));
+  LC_CUDA(cudaStreamSynchronize(s));
+  return (lc_status)verdict;
+}
+
+lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_host,
+                            lc_mode m, void* stream) {
+  if (!ctx || (!reqs && count) || (!status_host && count)) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  if (count == 0) return LC_OK;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const lc_params& p = ctx->params;
+
+  // Bytes each request will write: its full result, clipped to out_cap.
+  std::vector<size_t> out_len(count);
+  for (size_t i = 0; i < count; i++) {
+    const lc_req& r = reqs[i];
+    size_t n = 0, olen = 0;
+    if (r.dir == LC_ENCRYPT) olen = ct_len(p, r.in_len, m);
+    else if (pt_len(p, r.in_len, m, &n)) olen = n;
+    out_len[i] = r.out ? std::min(olen, r.out_cap) : 0;
+  }
+
+  // Requests whose host buffers follow each other are copied as one run.
+  // Each run lands in the device staging area at the same address modulo
+  // 256 as on the host, so the kernel's 16-byte vector path applies
+  // whenever it would for the host buffers.
+  struct Run {
+    size_t first, last;
+    const uint8_t* h;
+    size_t span, dev_off;
+  };
+  size_t cursor = 0;
+  auto plan = [&](bool input, std::vector<Run>& runs) {
+    for (size_t i = 0; i < count;) {
+      const uint8_t* h = input ? reqs[i].in : reqs[i].out;
+      size_t span = input ? reqs[i].in_len : out_len[i];
+      size_t j = i + 1;
+      while (h && j < count) {
+        const uint8_t* hj = input ? reqs[j].in : reqs[j].out;
+        if (hj != h + span) break;
+        span += input ? reqs[j].in_len : out_len[j];
+        j++;
+      }
+      cursor = (cursor + 255) & ~(size_t)255;
+      const size_t off = cursor + (reinterpret_cast<uintptr_t>(h) & 255u);
+      runs.push_back(Run{i, j, h, span, off});
+      cursor = off + span;
+      i = j;
+    }
+  };
+  std::vector<Run> in_runs, out_runs;
+  plan(true, in_runs);
+  plan(false, out_runs);
+  lc_status st = grow_device(&ctx->io_dev, &ctx->io_cap, std::max<size_t>(cursor, 256), nullptr);
+  if (st != LC_OK) return st;
+  st = ensure_status_tmp(ctx, count);
+  if (st != LC_OK) return st;
+
+  std::vector<lc_req> dreq(reqs, reqs + count);
+  for (const Run& r : in_runs) {
+    if (r.h && r.span)
+      LC_CUDA(cudaMemcpyAsync(ctx->io_dev + r.dev_off, r.h, r.span, cudaMemcpyHostToDevice, s));
+    for (size_t k = r.first; k < r.last; k++)
+      dreq[k].in = r.h ? ctx->io_dev + r.dev_off + (reqs[k].in - r.h) : nullptr;
+  }
+  for (const Run& r : out_runs)
+    for (size_t k = r.first; k < r.last; k++) {
+      dreq[k].out = r.h ? ctx->io_dev + r.dev_off + (reqs[k].out - r.h) : nullptr;
+      dreq[k].out_cap = out_len[k] < reqs[k].out_cap ? out_len[k] : reqs[k].out_cap;
+    }
+  st = run_batch_impl(ctx, dreq.data(), count, ctx->status_tmp_dev, m, s);
+  if (st != LC_OK) return st;
+  for (const Run& r : out_runs)
+    if (r.h && r.span)
+      LC_CUDA(cudaMemcpyAsync(const_cast<uint8_t*>(r.h), ctx->io_dev + r.dev_off, r.span,
+                              cudaMemcpyDeviceToHost, s));
+  LC_CUDA(cudaMemcpyAsync(status_host, ctx->status_tmp_dev, count * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, s));
+  LC_CUDA(cudaStreamSynchronize(s));
+  return LC_OK;
+}
+
+lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out) {
+  if (!ctx || !out) return LC_ERR_ARG;
+  *out = ctx->launch;
+  return LC_OK;
+}
+
+lc_status lc_ctx_set_launch(lc_ctx* ctx, const lc_launch* l) {
+  if (!ctx || !l) return LC_ERR_ARG;
+  if (l->threads_per_cta < 32 || l->threads_per_cta > 256 || l->threads_per_cta % 32) return LC_ERR_ARG;
+  if (l->ctas_per_sm > 64 || l->smem_staging > 1) return LC_ERR_ARG;
+  ctx->launch = *l;
+  ctx->launch.reserved = 0;
+  ctx->graph_valid = false;
+  return LC_OK;
+}
+
+lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best) {
+  if (!ctx) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (probe_bytes == 0) probe_bytes = (size_t)64 << 20;
+  const lc_params& p = ctx->params;
+  const size_t nparts = std::max<size_t>(1, probe_bytes / p.block_len);
+  const size_t n = nparts * p.block_len;
+  uint8_t* buf = nullptr;
+  LC_CUDA(cudaMalloc(&buf, n + ct_len(p, n, LC_PARALLEL)));
+  uint8_t* in = buf;
+  uint8_t* out = buf + n;
+  lc_status st = cuda_fail(launch_synth(in, n, 0x7E57ull, 0, s));
+  const uint8_t pw[16] = {'a', 'u', 't', 'o', 't', 'u', 'n', 'e', '-', 'p', 'r', 'o', 'b', 'e', '!', '!'};
+  lc_req r{pw, 16, LC_ENCRYPT, in, n, out, ct_len(p, n, LC_PARALLEL)};
+  lc_launch saved = ctx->launch, bestl = ctx->launch;
+  double best_ms = 1e300;
+  const uint32_t tpcs[] = {64, 128, 256};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e0));
+  if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e1));
+  for (uint32_t tpc : tpcs) {
+    if (st != LC_OK) break;
+    const int maxc = resident_ctas(ctx, (int)tpc);
+    std::vector<uint32_t> cands = {0};
+    for (uint32_t c = 1; c < (uint32_t)maxc; c *= 2) cands.push_back(c);
+    for (uint32_t c : cands) {
+      lc_launch l{tpc, c, 0, 0};
+      ctx->launch = l;
+      ctx->graph_valid = false;
+      int32_t* stat = nullptr;
+      st = ensure_status_tmp(ctx, 1);
+      if (st != LC_OK) break;
+      stat = ctx->status_tmp_dev;
+      st = run_batch_impl(ctx, &r, 1, stat, LC_PARALLEL, s);  // warm-up / graph build
+      if (st != LC_OK) break;
+      st = cuda_fail(cudaEventRecord(e0, s));
+      if (st == LC_OK) st = run_batch_impl(ctx, &r, 1, stat, LC_PARALLEL, s);
+      if (st == LC_OK) st = cuda_fail(cudaEventRecord(e1, s));
+      if (st == LC_OK) st = cuda_fail(cudaEventSynchronize(e1));
+      float ms = 0;
+      if (st == LC_OK) st = cuda_fail(cudaEventElapsedTime(&ms, e0, e1));
+      if (st == LC_OK && ms < best_ms) {
+        best_ms = ms;
+        bestl = l;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  ctx->launch = (st == LC_OK) ? bestl : saved;
+  ctx->graph_valid = false;
+  if (best) *best = ctx->launch;
+  return st;
+}
+
+lc_status lc_ctx_timing(lc_ctx* ctx, int enable) {
+  if (!ctx) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  lc_status st = drain_timing(ctx);
+  ctx->timing = enable != 0;
+  ctx->total_ms = 0.0;
+  ctx->timed_launches = 0;
+  return st;
+}
+
+lc_status lc_ctx_kernel_time(lc_ctx* ctx, double* total_ms, uint64_t* launches) {
+  if (!ctx) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  lc_status st = drain_timing(ctx);
+  if (total_ms) *total_ms = ctx->total_ms;
+  if (launches) *launches = ctx->timed_launches;
+  return st;
+}
+
+uint64_t lc_ctx_launch_count(const lc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lc_status lc_key_info(const lc_params* p, const uint8_t* pw, size_t pw_len, lc_key_info_t* out) {
+  if (!out) return LC_ERR_ARG;
+  lc_params prm;
+  if (p) prm = *p; else lc_params_default(&prm);
+  if (!params_valid(prm)) return LC_ERR_ARG;
+  HostKey k;
+  lc_status st = key_schedule(prm, pw, pw_len, &k);
+  if (st != LC_OK) return st;
+  for (int i = 0; i < 3; i++) {
+    out->aprime[i] = k.aprime[i];
+    out->mu[i] = k.mu[i];
+    out->omega[i] = k.omega[i];
+  }
+  out->L = k.L;
+  out->D = k.D;
+  return LC_OK;
+}
+
+lc_status lc_plan_batch(const lc_params* p, const lc_req* reqs, size_t count, lc_mode m,
+                        int32_t* init_status, uint64_t* nrows) {
+  if ((!reqs || !init_status) && count) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  lc_params prm;
+  if (p) prm = *p; else lc_params_default(&prm);
+  if (!params_valid(prm)) return LC_ERR_ARG;
+  uint64_t rows = 0;
+  for (size_t i = 0; i < count; i++) {
+    size_t n = 0;
+    init_status[i] = validate_req(prm, reqs[i], m, &n);
+    if (init_status[i] == LC_OK) rows += nblocks_of(prm, n, m);
+  }
+  if (nrows) *nrows = rows;
+  return LC_OK;
+}
+
+lc_status lc_synth_uniform(uint8_t* dst_dev, size_t n, uint64_t seed, uint64_t offset, void* stream) {
+  if (n && !dst_dev) return LC_ERR_ARG;
+  return cuda_fail(launch_synth(dst_dev, n, seed, offset, static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

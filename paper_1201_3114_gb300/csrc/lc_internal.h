@@ -1,0 +1,66 @@
+// lc_internal.h -- structures shared by the host side of liblorenzcipher and
+// its CUDA kernels.  Nothing here is part of the public ABI (include/lc.h).
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/lc.h"
+
+namespace lc {
+
+// Largest Omega bound supported (Eq. 7 allows k_i <= 4 for xi = 52; the
+// library accepts up to 8, i.e. any byte of the int64).
+constexpr int kMaxK = 8;
+// Theta table: Theta[w][P] = P / 10^(3 + w), w < kMaxK, P < 256 (Sec. 3.2 Step 2).
+constexpr int kThetaEntries = kMaxK * 256;
+
+// Constants of the method as the kernels read them.
+struct DevParams {
+  double sigma, rho, beta, dt, eta;
+  uint32_t n_warm;
+  uint32_t steps_per_byte;
+  uint32_t block_len;
+  uint32_t tag_len;
+  uint32_t k[3];
+  uint32_t k_all4;  // 1 when k = (4, 4, 4): Omega fits in two bits
+};
+
+// One message of a batch, as the kernels see it (80 bytes).
+struct alignas(16) DevMsg {
+  const uint8_t* in;   // plaintext (encrypt) or ciphertext (decrypt)
+  uint8_t* out;        // ciphertext (encrypt) or plaintext (decrypt)
+  uint64_t n;          // plaintext length in bytes
+  double base[3];      // RN(a'_j + lambda_j): Eq. 5 without the part offset
+  double aprime[3];    // a'_j, added after every byte (Step 3)
+  uint32_t key_bits;   // mu_i in bits [2i, 2i+2), Omega_i in bits [8+4i, 12+4i)
+  uint32_t flags;      // kFlagDecrypt | kFlagSequential
+};
+static_assert(sizeof(DevMsg) == 80, "DevMsg layout");
+
+constexpr uint32_t kFlagDecrypt = 1u;
+constexpr uint32_t kFlagSequential = 2u;
+
+// One trajectory: part `b` of message `msg` (b = 0 in sequential mode).
+struct DevRow {
+  uint32_t msg;
+  uint32_t b;
+};
+
+// Batch header, at the start of the uploaded workspace.
+struct alignas(16) DevHeader {
+  uint32_t nrows;
+  uint32_t nmsgs;
+  int32_t* status_out;  // caller's status array (device)
+  uint64_t reserved[2];
+};
+static_assert(sizeof(DevHeader) == 32, "DevHeader layout");
+
+// Persistent-kernel scratch that lives across launches: the row counter and
+// the per-message fail flags.  The finalize kernel clears both after use.
+struct DevScratch {
+  uint32_t row_counter;
+  uint32_t pad[3];
+};
+
+}  // namespace lc

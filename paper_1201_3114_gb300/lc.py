@@ -1,0 +1,434 @@
+"""Python binding of liblorenzcipher (include/lc.h).
+
+Argument marshalling only: every step of the cipher runs in the library's
+CUDA kernels.  Functions keep the C names (lc_encrypt, lc_decrypt,
+lc_run_batch, ...); device buffers are PyTorch CUDA tensors (or raw device
+addresses) and streams are ``torch.cuda.Stream`` objects (or raw
+``cudaStream_t`` values).  There is no CPU fallback: if the shared library
+cannot be built or loaded, :func:`load` raises.
+"""
+import ctypes as C
+import os
+import re
+import threading
+
+from . import build as _build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lc.h")
+
+LC_OK, LC_ERR_ARG, LC_ERR_PASSWORD, LC_ERR_LENGTH, LC_ERR_INTEGRITY = 0, 1, 2, 3, 4
+LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_NOMEM = 5, 6, 7
+LC_PARALLEL, LC_SEQUENTIAL = 0, 1
+LC_ENCRYPT, LC_DECRYPT = 0, 1
+
+
+class lc_params(C.Structure):
+    _fields_ = [
+        ("sigma", C.c_double),
+        ("rho", C.c_double),
+        ("beta", C.c_double),
+        ("dt", C.c_double),
+        ("n_warm", C.c_uint32),
+        ("steps_per_byte", C.c_uint32),
+        ("lam", C.c_double * 3),
+        ("k", C.c_uint32 * 3),
+        ("block_len", C.c_uint32),
+        ("tag_len", C.c_uint32),
+        ("eta", C.c_double),
+    ]
+
+
+class lc_req(C.Structure):
+    _fields_ = [
+        ("pw", C.c_void_p),
+        ("pw_len", C.c_uint32),
+        ("dir", C.c_uint32),
+        ("inp", C.c_void_p),
+        ("in_len", C.c_size_t),
+        ("out", C.c_void_p),
+        ("out_cap", C.c_size_t),
+    ]
+
+
+class lc_launch(C.Structure):
+    _fields_ = [
+        ("threads_per_cta", C.c_uint32),
+        ("ctas_per_sm", C.c_uint32),
+        ("smem_staging", C.c_uint32),
+        ("reserved", C.c_uint32),
+    ]
+
+
+class lc_key_info_t(C.Structure):
+    _fields_ = [
+        ("aprime", C.c_double * 3),
+        ("mu", C.c_uint32 * 3),
+        ("omega", C.c_uint32 * 3),
+        ("L", C.c_uint32),
+        ("D", C.c_uint32),
+    ]
+
+
+class lc_pipe_rates(C.Structure):
+    _fields_ = [
+        ("dadd_gops", C.c_double),
+        ("dmul_gops", C.c_double),
+        ("cvt_gops", C.c_double),
+        ("imad_gops", C.c_double),
+        ("ialu_gops", C.c_double),
+        ("ffma_gops", C.c_double),
+        ("sm_clock_mhz", C.c_double),
+        ("sm_count", C.c_uint32),
+        ("reserved", C.c_uint32),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class LcError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, status_string(status), status))
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGNATURES = {
+    "lc_version": (C.c_uint32, []),
+    "lc_status_string": (C.c_char_p, [C.c_int]),
+    "lc_params_default": (C.c_int, [C.POINTER(lc_params)]),
+    "lc_ctx_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "lc_ctx_destroy": (None, [C.c_void_p]),
+    "lc_ctx_set_params": (C.c_int, [C.c_void_p, C.POINTER(lc_params)]),
+    "lc_ctx_get_params": (C.c_int, [C.c_void_p, C.POINTER(lc_params)]),
+    "lc_ciphertext_len": (C.c_size_t, [C.c_void_p, C.c_size_t, C.c_int]),
+    "lc_plaintext_len": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.POINTER(C.c_size_t)]),
+    "lc_encrypt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                             C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
+    "lc_decrypt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                             C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
+    "lc_run_batch": (C.c_int, [C.c_void_p, C.POINTER(lc_req), C.c_size_t, C.c_void_p, C.c_int,
+                               C.c_void_p]),
+    "lc_run_batch_host": (C.c_int, [C.c_void_p, C.POINTER(lc_req), C.c_size_t, C.c_void_p,
+                                    C.c_int, C.c_void_p]),
+    "lc_ctx_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lc_launch)]),
+    "lc_ctx_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lc_launch)]),
+    "lc_tune": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(lc_launch)]),
+    "lc_ctx_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "lc_ctx_kernel_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+    "lc_ctx_launch_count": (C.c_uint64, [C.c_void_p]),
+    "lc_key_info": (C.c_int, [C.POINTER(lc_params), C.c_void_p, C.c_size_t,
+                              C.POINTER(lc_key_info_t)]),
+    "lc_plan_batch": (C.c_int, [C.POINTER(lc_params), C.POINTER(lc_req), C.c_size_t, C.c_int,
+                                C.c_void_p, C.POINTER(C.c_uint64)]),
+    "lc_probe_pipes": (C.c_int, [C.c_int, C.POINTER(lc_pipe_rates)]),
+    "lc_synth_uniform": (C.c_int, [C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint64, C.c_void_p]),
+}
+
+
+def header_symbols():
+    """Every function the public header declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lc_[a-z0-9_]+)\s*\(", text)))
+
+
+def load():
+    """Build if needed and load the shared library (raises on failure)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("liblorenzcipher.so is missing at %s" % path)
+            lib = C.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def library_path():
+    return _build.LIB_PATH
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _ptr(x):
+    """Device/host address of a tensor, or an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr() if x.numel() else None
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data if x.size else None
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _nbytes(x):
+    if hasattr(x, "numel"):
+        return x.numel() * x.element_size()
+    if hasattr(x, "nbytes"):
+        return x.nbytes
+    raise TypeError("cannot size %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _pwbuf(pw):
+    if isinstance(pw, str):
+        pw = pw.encode("latin-1")
+    pw = bytes(pw)
+    buf = C.create_string_buffer(pw, max(1, len(pw)))
+    return buf, len(pw)
+
+
+def status_string(status: int) -> str:
+    return load().lc_status_string(status).decode()
+
+
+def check(status, what="liblorenzcipher"):
+    if status != LC_OK:
+        raise LcError(status, what)
+    return status
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------
+
+def lc_version() -> int:
+    return load().lc_version()
+
+
+def lc_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def lc_params_default() -> lc_params:
+    p = lc_params()
+    check(load().lc_params_default(C.byref(p)), "lc_params_default")
+    return p
+
+
+def params(**over) -> lc_params:
+    """Default parameters with field overrides (``lam``/``k`` take 3-sequences)."""
+    p = lc_params_default()
+    for k, v in over.items():
+        if k in ("lam", "k"):
+            arr = getattr(p, k)
+            for i in range(3):
+                arr[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def lc_ctx_create(device: int = 0) -> int:
+    h = C.c_void_p()
+    check(load().lc_ctx_create(device, C.byref(h)), "lc_ctx_create")
+    return h.value
+
+
+def lc_ctx_destroy(ctx) -> None:
+    load().lc_ctx_destroy(ctx)
+
+
+def lc_ctx_set_params(ctx, p: lc_params) -> int:
+    return load().lc_ctx_set_params(ctx, C.byref(p))
+
+
+def lc_ctx_get_params(ctx) -> lc_params:
+    p = lc_params()
+    check(load().lc_ctx_get_params(ctx, C.byref(p)), "lc_ctx_get_params")
+    return p
+
+
+def lc_ciphertext_len(ctx, n: int, mode: int = LC_PARALLEL) -> int:
+    return load().lc_ciphertext_len(ctx, n, mode)
+
+
+def lc_plaintext_len(ctx, c_len: int, mode: int = LC_PARALLEL):
+    n = C.c_size_t()
+    st = load().lc_plaintext_len(ctx, c_len, mode, C.byref(n))
+    return n.value if st == LC_OK else None
+
+
+def lc_encrypt(ctx, pw, P, n, Cbuf, c_cap, mode=LC_PARALLEL, stream=None) -> int:
+    buf, L = _pwbuf(pw)
+    return load().lc_encrypt(ctx, buf, L, _ptr(P), n, _ptr(Cbuf), c_cap, mode, _stream(stream))
+
+
+def lc_decrypt(ctx, pw, Cbuf, c_len, P, p_cap, mode=LC_PARALLEL, stream=None) -> int:
+    buf, L = _pwbuf(pw)
+    return load().lc_decrypt(ctx, buf, L, _ptr(Cbuf), c_len, _ptr(P), p_cap, mode, _stream(stream))
+
+
+class Batch:
+    """An lc_req array plus the password buffers it points to."""
+
+    def __init__(self, items):
+        """items: iterable of (pw, dir, in, in_len, out, out_cap)."""
+        items = list(items)
+        self._pw = []
+        self.reqs = (lc_req * max(1, len(items)))()
+        self.count = len(items)
+        for i, (pw, d, inp, in_len, out, out_cap) in enumerate(items):
+            buf, L = _pwbuf(pw)
+            self._pw.append(buf)
+            r = self.reqs[i]
+            r.pw = C.cast(buf, C.c_void_p)
+            r.pw_len = L
+            r.dir = d
+            r.inp = _ptr(inp)
+            r.in_len = in_len
+            r.out = _ptr(out)
+            r.out_cap = out_cap
+
+
+def lc_run_batch(ctx, batch: Batch, status_dev, mode=LC_PARALLEL, stream=None) -> int:
+    return load().lc_run_batch(ctx, batch.reqs, batch.count, _ptr(status_dev), mode, _stream(stream))
+
+
+def lc_run_batch_host(ctx, batch: Batch, status_host, mode=LC_PARALLEL, stream=None) -> int:
+    return load().lc_run_batch_host(ctx, batch.reqs, batch.count, _ptr(status_host), mode,
+                                    _stream(stream))
+
+
+def lc_ctx_get_launch(ctx) -> lc_launch:
+    l = lc_launch()
+    check(load().lc_ctx_get_launch(ctx, C.byref(l)), "lc_ctx_get_launch")
+    return l
+
+
+def lc_ctx_set_launch(ctx, threads_per_cta=256, ctas_per_sm=0, smem_staging=0) -> int:
+    l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, 0)
+    return load().lc_ctx_set_launch(ctx, C.byref(l))
+
+
+def lc_tune(ctx, probe_bytes=0, stream=None) -> lc_launch:
+    l = lc_launch()
+    check(load().lc_tune(ctx, probe_bytes, _stream(stream), C.byref(l)), "lc_tune")
+    return l
+
+
+def lc_ctx_timing(ctx, enable: bool) -> int:
+    return load().lc_ctx_timing(ctx, 1 if enable else 0)
+
+
+def lc_ctx_kernel_time(ctx):
+    ms = C.c_double()
+    n = C.c_uint64()
+    check(load().lc_ctx_kernel_time(ctx, C.byref(ms), C.byref(n)), "lc_ctx_kernel_time")
+    return ms.value, n.value
+
+
+def lc_ctx_launch_count(ctx) -> int:
+    return load().lc_ctx_launch_count(ctx)
+
+
+def lc_key_info(pw, p: lc_params = None):
+    buf, L = _pwbuf(pw)
+    out = lc_key_info_t()
+    st = load().lc_key_info(C.byref(p) if p is not None else None, buf, L, C.byref(out))
+    return st, out
+
+
+def lc_plan_batch(batch: Batch, mode=LC_PARALLEL, p: lc_params = None):
+    import numpy as np
+    st = np.zeros(max(1, batch.count), dtype=np.int32)
+    rows = C.c_uint64()
+    rc = load().lc_plan_batch(C.byref(p) if p is not None else None, batch.reqs, batch.count, mode,
+                              st.ctypes.data, C.byref(rows))
+    return rc, st[:batch.count], rows.value
+
+
+def lc_probe_pipes(device: int = 0) -> lc_pipe_rates:
+    r = lc_pipe_rates()
+    check(load().lc_probe_pipes(device, C.byref(r)), "lc_probe_pipes")
+    return r
+
+
+def lc_synth_uniform(dst, n, seed, offset=0, stream=None) -> int:
+    return load().lc_synth_uniform(_ptr(dst), n, seed & ((1 << 64) - 1), offset, _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# convenience layer over the same entry points
+# ---------------------------------------------------------------------------
+
+class Context:
+    """Owns an lc_ctx; encrypt/decrypt PyTorch CUDA uint8 tensors."""
+
+    def __init__(self, device: int = 0, params_: lc_params = None):
+        self.handle = lc_ctx_create(device)
+        self.device = device
+        if params_ is not None:
+            check(lc_ctx_set_params(self.handle, params_), "lc_ctx_set_params")
+
+    def close(self):
+        if self.handle:
+            lc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def ciphertext_len(self, n, mode=LC_PARALLEL):
+        return lc_ciphertext_len(self.handle, n, mode)
+
+    def plaintext_len(self, c_len, mode=LC_PARALLEL):
+        return lc_plaintext_len(self.handle, c_len, mode)
+
+    def encrypt(self, pw, P, mode=LC_PARALLEL, stream=None, out=None):
+        import torch
+        n = P.numel()
+        c_len = self.ciphertext_len(n, mode)
+        if out is None:
+            out = torch.empty(c_len, dtype=torch.uint8, device=P.device if n else "cuda")
+        check(lc_encrypt(self.handle, pw, P, n, out, _nbytes(out), mode, stream), "lc_encrypt")
+        return out
+
+    def decrypt(self, pw, Cbuf, mode=LC_PARALLEL, stream=None, out=None):
+        """(status, plaintext tensor); status LC_ERR_INTEGRITY leaves it zeroed."""
+        import torch
+        c_len = Cbuf.numel()
+        n = self.plaintext_len(c_len, mode)
+        if n is None:
+            raise LcError(LC_ERR_LENGTH, "lc_decrypt")
+        if out is None:
+            out = torch.empty(max(n, 0), dtype=torch.uint8, device=Cbuf.device)
+        st = lc_decrypt(self.handle, pw, Cbuf, c_len, out, _nbytes(out), mode, stream)
+        if st not in (LC_OK, LC_ERR_INTEGRITY):
+            raise LcError(st, "lc_decrypt")
+        return st, out

@@ -1,0 +1,422 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Every comparison is bit-exact (tolerance 0): the outputs are bytes and
+verdicts, and the trajectory arithmetic is required to round exactly as
+the oracle does.  Inputs are seeded and synthetic (paper_1201_3114_gb300.synth).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1201_3114_gb300 import lc, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+B = 4096
+T = 8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = lc.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint8)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def gpu_encrypt(ctx, pw, P, mode=lc.LC_PARALLEL):
+    return host(ctx.encrypt(pw, dev(P), mode))
+
+
+def gpu_decrypt(ctx, pw, Cb, mode=lc.LC_PARALLEL):
+    st, out = ctx.decrypt(pw, dev(Cb), mode)
+    return st, host(out)
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def test_device_generator_matches_host():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    for seed in (1234567, synth.config_seed(3)):
+        for off in (0, 1, 3, 8, 13, 4096 * 7 + 5):
+            for n in (1, 7, 8, 9, 100, 4096, 65536 + 3):
+                buf = torch.empty(n + 16, dtype=torch.uint8, device="cuda")
+                for shift in (0, 3):
+                    lc.check(lc.lc_synth_uniform(buf[shift:].data_ptr(), n, seed, off))
+                    got = host(buf)[shift:shift + n]
+                    assert np.array_equal(got, synth.uniform_bytes(seed, n, off)), (seed, off, n, shift)
+
+
+# ---------------------------------------------------------------------------
+# single messages
+# ---------------------------------------------------------------------------
+
+def test_config1_64k(ctx):
+    c = synth.cfg1()
+    want = O.encrypt(c["pw"], c["P"], O.PARALLEL)
+    got = gpu_encrypt(ctx, c["pw"], c["P"])
+    assert np.array_equal(got, want)
+    st, back = gpu_decrypt(ctx, c["pw"], got)
+    assert st == lc.LC_OK and np.array_equal(back, c["P"])
+
+
+SIZES = [0, 1, 2, 15, 16, 17, 31, 33, 255, B - 1, B, B + 1, B + 16, 2 * B - 3, 3 * B + 5]
+
+
+@pytest.mark.parametrize("mode", [lc.LC_PARALLEL, lc.LC_SEQUENTIAL])
+def test_edge_sizes(ctx, mode):
+    for i, n in enumerate(SIZES):
+        pw = synth.password(synth.subseed(40, i), 1 + (5 * i) % 32)
+        P = synth.uniform_bytes(synth.subseed(41, i), n)
+        want = O.encrypt(pw, P, mode)
+        got = gpu_encrypt(ctx, pw, P, mode)
+        assert np.array_equal(got, want), (n, mode)
+        st, back = gpu_decrypt(ctx, pw, got, mode)
+        assert st == lc.LC_OK and np.array_equal(back, P), (n, mode)
+
+
+def test_every_password_length(ctx):
+    P = synth.uniform_bytes(42, 3 * B + 77)
+    for length in range(1, 33):
+        pw = synth.password(synth.subseed(43, length), length)
+        assert np.array_equal(gpu_encrypt(ctx, pw, P), O.encrypt(pw, P)), length
+    for pw in (b"\x00\x00\x00", b"\xff" * 32, b"\x80"):
+        assert np.array_equal(gpu_encrypt(ctx, pw, P), O.encrypt(pw, P)), pw
+
+
+def test_unaligned_buffers(ctx):
+    # Misaligned input or output pointers take the byte path; results agree.
+    n = 2 * B + 21
+    P = synth.uniform_bytes(44, n)
+    pw = b"unaligned-buffers"
+    want = O.encrypt(pw, P)
+    for pin, pout in ((1, 0), (0, 3), (5, 7), (16, 16)):
+        src = torch.zeros(n + 64, dtype=torch.uint8, device="cuda")
+        dst = torch.zeros(want.size + 64, dtype=torch.uint8, device="cuda")
+        src[pin:pin + n] = dev(P)
+        st = lc.lc_encrypt(ctx.handle, pw, src.data_ptr() + pin, n, dst.data_ptr() + pout,
+                           want.size, lc.LC_PARALLEL)
+        assert st == lc.LC_OK
+        got = host(dst)[pout:pout + want.size]
+        assert np.array_equal(got, want), (pin, pout)
+        back = torch.zeros(n + 64, dtype=torch.uint8, device="cuda")
+        st = lc.lc_decrypt(ctx.handle, pw, dst.data_ptr() + pout, want.size, back.data_ptr() + pin,
+                           n, lc.LC_PARALLEL)
+        assert st == lc.LC_OK and np.array_equal(host(back)[pin:pin + n], P)
+
+
+def test_in_place(ctx):
+    n = 3 * B + 9
+    P = synth.uniform_bytes(45, n)
+    pw = b"in-place"
+    want = O.encrypt(pw, P)
+    buf = torch.zeros(want.size, dtype=torch.uint8, device="cuda")
+    buf[:n] = dev(P)
+    assert lc.lc_encrypt(ctx.handle, pw, buf, n, buf, want.size, lc.LC_PARALLEL) == lc.LC_OK
+    assert np.array_equal(host(buf), want)
+    assert lc.lc_decrypt(ctx.handle, pw, buf, want.size, buf, n, lc.LC_PARALLEL) == lc.LC_OK
+    assert np.array_equal(host(buf)[:n], P)
+
+
+def test_config2_text_both_modes_and_tamper(ctx):
+    c = synth.cfg2()
+    P, pw = c["P"], c["pw"]
+    for mode in (lc.LC_PARALLEL, lc.LC_SEQUENTIAL):
+        want = O.encrypt(pw, P, mode)
+        got = gpu_encrypt(ctx, pw, P, mode)
+        assert np.array_equal(got, want), mode
+        st, back = gpu_decrypt(ctx, pw, got, mode)
+        assert st == lc.LC_OK and np.array_equal(back, P)
+        pos = synth.word(c["flip_seed"], mode) % got.size
+        bad = got.copy()
+        bad[pos] ^= 1 + synth.word(c["flip_seed"], 10 + mode) % 255
+        st, out = gpu_decrypt(ctx, pw, bad, mode)
+        assert st == lc.LC_ERR_INTEGRITY and not out.any()
+        ost, oout = O.decrypt(pw, bad, mode)
+        assert ost == O.ERR_INTEGRITY
+
+
+def test_wrong_password_rejected(ctx):
+    P = synth.uniform_bytes(46, 5 * B)
+    ct = gpu_encrypt(ctx, "123456", P)
+    st, out = gpu_decrypt(ctx, "123457", ct)
+    assert st == lc.LC_ERR_INTEGRITY and not out.any()
+
+
+def test_tamper_every_tag_byte_and_random_body_bytes(ctx):
+    # One batch decrypts many tampered copies; each must be rejected, the
+    # untouched copy accepted, exactly as the oracle decides.
+    pw = b"tamper"
+    n = 2 * B + 50
+    P = synth.uniform_bytes(47, n)
+    ct = O.encrypt(pw, P)
+    rng = np.random.default_rng(48)
+    positions = list(range(n, ct.size)) + [int(x) for x in rng.integers(0, n, 300)]
+    copies = np.tile(ct, (len(positions) + 1, 1))
+    for k, pos in enumerate(positions):
+        copies[k, pos] ^= int(rng.integers(1, 256))
+    cin = dev(copies)
+    pout = torch.zeros((len(positions) + 1, n), dtype=torch.uint8, device="cuda")
+    items = [(pw, lc.LC_DECRYPT, cin[k], ct.size, pout[k], n) for k in range(len(positions) + 1)]
+    status = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+    b = lc.Batch(items)
+    lc.check(lc.lc_run_batch(ctx.handle, b, status))
+    st = host(status)
+    outs = host(pout)
+    assert all(s == lc.LC_ERR_INTEGRITY for s in st[:-1])
+    assert st[-1] == lc.LC_OK and np.array_equal(outs[-1], P)
+    assert not outs[:-1].any()
+
+
+# ---------------------------------------------------------------------------
+# other parameter profiles (general-k path, several Euler steps per byte,
+# divergent dt, small parts)
+# ---------------------------------------------------------------------------
+
+PROFILES = [
+    dict(dt=0.027),                      # leaves the basin: NaN/inf saturation
+    dict(k=(3, 4, 4)),                   # general Omega path
+    dict(k=(8, 5, 1)),
+    dict(steps_per_byte=3),
+    dict(n_warm=0),
+    dict(block_len=64, tag_len=3),
+    dict(lam=(-15.0, -11.0, 61.0), eta=2.0 ** -10),
+    dict(sigma=0.0, rho=0.0, beta=0.0, dt=0.0, lam=(1.5, 1.5, 1.5)),
+]
+
+
+@pytest.mark.parametrize("over", PROFILES, ids=lambda d: ",".join(d))
+def test_parameter_profiles(over):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    po = O.params(**over)
+    pl = lc.params(**over)
+    with lc.Context(0, pl) as c:
+        for i, n in enumerate([0, 1, 17, 63, 64, 65, 2 * B + 3]):
+            for mode in (lc.LC_PARALLEL, lc.LC_SEQUENTIAL):
+                pw = synth.password(synth.subseed(49, i), 3 + i)
+                P = synth.uniform_bytes(synth.subseed(50, i), n)
+                want = O.encrypt(pw, P, mode, po)
+                got = gpu_encrypt(c, pw, P, mode)
+                assert np.array_equal(got, want), (over, n, mode)
+                st, back = gpu_decrypt(c, pw, got, mode)
+                assert st == lc.LC_OK and np.array_equal(back, P)
+
+
+# ---------------------------------------------------------------------------
+# batched path
+# ---------------------------------------------------------------------------
+
+def _mixed_batch(count, seed, max_size=40000):
+    rng = np.random.default_rng(seed)
+    msgs = []
+    for m in range(count):
+        n = int(rng.choice([0, 1, 15, 16, int(rng.integers(1, max_size)), B, B + 1]))
+        pw = synth.password(synth.subseed(seed, m), int(rng.integers(1, 33)))
+        P = synth.uniform_bytes(synth.subseed(seed + 1, m), n)
+        d = int(rng.integers(0, 2))
+        msgs.append((pw, d, P))
+    return msgs
+
+
+@pytest.mark.parametrize("mode", [lc.LC_PARALLEL, lc.LC_SEQUENTIAL])
+def test_batch_mixed_matches_oracle_and_alone(ctx, mode):
+    msgs = _mixed_batch(96, 51)
+    items, expect, keep = [], [], []
+    for pw, d, P in msgs:
+        ct = O.encrypt(pw, P, mode)
+        if d == lc.LC_ENCRYPT:
+            src, want = dev(P), ct
+        else:
+            src, want = dev(ct), P
+        out = torch.zeros(max(1, want.size), dtype=torch.uint8, device="cuda")
+        keep += [src, out]
+        items.append((pw, d, src, src.numel() if (d or P.size) else 0, out, want.size))
+        expect.append(want)
+    status = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+    lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(items), status, mode))
+    st = host(status)
+    assert all(s == lc.LC_OK for s in st)
+    for k, want in enumerate(expect):
+        got = host(items[k][4])[:want.size]
+        assert np.array_equal(got, want), k
+    # each message alone gives the same bytes as in the mix
+    for k in range(0, len(items), 7):
+        pw, d, src, ln, _, cap = items[k]
+        out = torch.zeros(max(1, cap), dtype=torch.uint8, device="cuda")
+        s1 = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        lc.check(lc.lc_run_batch(ctx.handle, lc.Batch([(pw, d, src, ln, out, cap)]), s1, mode))
+        assert host(s1)[0] == lc.LC_OK
+        assert np.array_equal(host(out)[:cap], expect[k])
+
+
+def test_batch_reports_per_request_errors(ctx):
+    P = synth.uniform_bytes(52, 1000)
+    pw = b"per-request"
+    ct = O.encrypt(pw, P)
+    src = dev(P)
+    csrc = dev(ct)
+    o1 = torch.zeros(ct.size, dtype=torch.uint8, device="cuda")
+    o2 = torch.zeros(ct.size, dtype=torch.uint8, device="cuda")
+    o3 = torch.zeros(P.size, dtype=torch.uint8, device="cuda")
+    bad = ct.copy()
+    bad[3] ^= 9
+    bsrc = dev(bad)
+    o4 = torch.ones(P.size, dtype=torch.uint8, device="cuda")
+    items = [
+        (pw, 0, src, P.size, o1, ct.size),          # ok
+        (b"", 0, src, P.size, o2, ct.size),         # bad password
+        (pw, 0, src, P.size, o2, ct.size - 1),      # too small
+        (pw, 1, csrc, ct.size, o3, P.size),         # ok
+        (pw, 1, bsrc, ct.size, o4, P.size),         # tampered
+        (pw, 1, csrc, T - 1, o3, P.size),           # shorter than one tag
+    ]
+    status = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+    lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(items), status))
+    assert list(host(status)) == [0, lc.LC_ERR_PASSWORD, lc.LC_ERR_LENGTH, 0, lc.LC_ERR_INTEGRITY,
+                                  lc.LC_ERR_LENGTH]
+    assert np.array_equal(host(o1), ct)
+    assert np.array_equal(host(o3), P)
+    assert not host(o4).any()
+
+
+def test_host_buffer_batch_equals_device_batch(ctx):
+    msgs = _mixed_batch(40, 53, max_size=20000)
+    # pack every input and output contiguously in pinned host memory
+    ins, outs = [], []
+    for pw, d, P in msgs:
+        ct = O.encrypt(pw, P)
+        ins.append(P if d == 0 else ct)
+        outs.append(ct if d == 0 else P)
+    hin = torch.empty(sum(x.size for x in ins), dtype=torch.uint8).pin_memory()
+    hout = torch.zeros(sum(x.size for x in outs), dtype=torch.uint8).pin_memory()
+    items, a, b_ = [], 0, 0
+    for (pw, d, _), x, y in zip(msgs, ins, outs):
+        hin[a:a + x.size] = torch.from_numpy(x)
+        items.append((pw, d, hin.data_ptr() + a, x.size, hout.data_ptr() + b_, y.size))
+        a += x.size
+        b_ += y.size
+    st = np.full(len(items), -1, dtype=np.int32)
+    lc.check(lc.lc_run_batch_host(ctx.handle, lc.Batch(items), st))
+    assert all(s == lc.LC_OK for s in st)
+    got = hout.numpy()
+    b_ = 0
+    for y in outs:
+        assert np.array_equal(got[b_:b_ + y.size], y)
+        b_ += y.size
+
+
+def test_launch_shapes_do_not_change_results(ctx):
+    n = 40 * B + 11
+    P = synth.uniform_bytes(54, n)
+    pw = b"launch-shapes"
+    want = O.encrypt(pw, P)
+    try:
+        for tpc, cps in ((32, 1), (64, 0), (128, 2), (256, 0)):
+            assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps) == lc.LC_OK
+            assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps)
+        best = lc.lc_tune(ctx.handle, 8 << 20)
+        assert best.threads_per_cta in (64, 128, 256)
+        assert np.array_equal(gpu_encrypt(ctx, pw, P), want)
+    finally:
+        lc.lc_ctx_set_launch(ctx.handle, 256, 0)
+
+
+def test_timing_and_launch_counters(ctx):
+    P = dev(synth.uniform_bytes(55, 8 * B))
+    lc.check(lc.lc_ctx_timing(ctx.handle, True))
+    before = lc.lc_ctx_launch_count(ctx.handle)
+    for _ in range(3):
+        ctx.encrypt(b"timing", P)
+    ms, n = lc.lc_ctx_kernel_time(ctx.handle)
+    assert n == 3 and ms > 0
+    assert lc.lc_ctx_launch_count(ctx.handle) - before == 6
+    lc.check(lc.lc_ctx_timing(ctx.handle, False))
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, sampled against the oracle
+# ---------------------------------------------------------------------------
+
+def test_config3_1gib_sampled(ctx):
+    spec = synth.cfg3_spec()
+    n, pw, seed = spec["n"], spec["pw"], spec["data_seed"]
+    P = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lc.check(lc.lc_synth_uniform(P, n, seed, 0))
+    Cd = ctx.encrypt(pw, P)
+    nb = n // B
+    key = O.key_schedule(pw)
+    rng = np.random.default_rng(56)
+    sample = sorted(set([0, 1, nb - 1] + [int(x) for x in rng.integers(0, nb, 40)]))
+    Ch = host(Cd)
+    for b in sample:
+        Pb = np.zeros(n, dtype=np.uint8)  # only block b's bytes are read
+        Pb[b * B:(b + 1) * B] = synth.uniform_bytes(seed, B, b * B)
+        Cb = np.zeros(n + T * nb, dtype=np.uint8)
+        O.encrypt_blocks(key, Pb, n, Cb, b, b + 1)
+        assert np.array_equal(Ch[b * B:(b + 1) * B], Cb[b * B:(b + 1) * B]), b
+        assert np.array_equal(Ch[n + T * b:n + T * b + T], Cb[n + T * b:n + T * b + T]), b
+    del Ch
+    st, back = ctx.decrypt(pw, Cd)
+    assert st == lc.LC_OK
+    assert torch.equal(back, P)
+
+
+def test_config4_batch_sampled(ctx):
+    spec = synth.cfg4_spec()
+    sizes, pws, seeds, dirs = spec["sizes"], spec["pws"], spec["data_seeds"], spec["dirs"]
+    count = len(sizes)
+    plains, cts = [], []
+    # seeded plaintexts made on the device; decrypt inputs are ciphertexts
+    for m in range(count):
+        p = torch.empty(int(sizes[m]), dtype=torch.uint8, device="cuda")
+        lc.check(lc.lc_synth_uniform(p, p.numel(), seeds[m], 0))
+        plains.append(p)
+    for m in range(count // 2, count):
+        cts.append(ctx.encrypt(pws[m], plains[m]))
+    items, outs = [], []
+    for m in range(count):
+        if dirs[m] == 0:
+            out = torch.empty(ctx.ciphertext_len(int(sizes[m])), dtype=torch.uint8, device="cuda")
+            items.append((pws[m], 0, plains[m], int(sizes[m]), out, out.numel()))
+        else:
+            c = cts[m - count // 2]
+            out = torch.empty(int(sizes[m]), dtype=torch.uint8, device="cuda")
+            items.append((pws[m], 1, c, c.numel(), out, out.numel()))
+        outs.append(out)
+    status = torch.full((count,), -1, dtype=torch.int32, device="cuda")
+    lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(items), status))
+    assert (host(status) == 0).all()
+    for m in range(count // 2, count):
+        assert torch.equal(outs[m], plains[m]), m
+    # encrypt outputs: small messages whole, large ones on sampled parts
+    rng = np.random.default_rng(57)
+    for m in sorted(set(int(x) for x in rng.integers(0, count // 2, 24))):
+        n = int(sizes[m])
+        P = synth.uniform_bytes(seeds[m], n)
+        got = host(outs[m])
+        if n <= 64 * 1024:
+            assert np.array_equal(got, O.encrypt(pws[m], P)), m
+        else:
+            key = O.key_schedule(pws[m])
+            nb = -(-n // B)
+            Cb = np.zeros(n + T * nb, dtype=np.uint8)
+            for b in (0, nb - 1, int(rng.integers(0, nb))):
+                O.encrypt_blocks(key, P, n, Cb, b, b + 1)
+                hi = min(n, (b + 1) * B)
+                assert np.array_equal(got[b * B:hi], Cb[b * B:hi]), (m, b)
+                assert np.array_equal(got[n + T * b:n + T * b + T], Cb[n + T * b:n + T * b + T])
