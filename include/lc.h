@@ -225,6 +225,43 @@ typedef struct {
 } lc_pipe_rates;
 lc_status lc_probe_pipes(int device, lc_pipe_rates* out);
 
+/* Allocation-free batched path.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they
+ * encrypt or decrypt -- for example code whose device memory is entirely
+ * owned by another allocator or memory pool (a cudaMalloc would fail or
+ * fragment that pool), code running inside an allocator's own callback or
+ * while holding its lock (a nested allocation would recurse or deadlock),
+ * and latency-critical threads that must not hit the device-wide
+ * synchronisation that cudaMalloc / cudaFree can imply.
+ *
+ * It runs the same persistent cipher kernel as lc_run_batch, with requests
+ * and results as there (device buffers, per-request status in status_dev),
+ * but without an lc_ctx and always with the default (v1) parameters.  All
+ * scratch memory the kernel needs beyond the caller's buffers -- the part
+ * table, the row counter, the per-request verdict flags and the Theta
+ * table -- sits in one fixed 2 MiB static device array inside the library,
+ * which every GPU that loads the library holds until the process exits.  No
+ * call allocates (no cudaMalloc, cudaFree, pinned host memory, graph or
+ * host heap).
+ *
+ * Limits: at most LC_NOALLOC_MAX_REQUESTS requests and LC_NOALLOC_MAX_PARTS
+ * parts (4096-byte parts in parallel mode, one per message in sequential
+ * mode; about 983 MB of parallel-mode data) per call; larger batches are
+ * rejected with LC_ERR_LENGTH before any GPU work.
+ *
+ * The first call on a device sets that device up (looks up the array's
+ * device address and copies the Theta table into it, synchronously); make
+ * that first call before any stream capture.  Every call uses the same
+ * array and leaves its contents behind; each call clears the counter and
+ * flags it needs.  Calls whose GPU work overlaps (for example on two
+ * streams without ordering between them) race on the array: issue them on
+ * one stream, or synchronise between them.  Asynchronous on `stream`; uses
+ * the current device.  Errors: LC_ERR_ARG, LC_ERR_LENGTH, LC_ERR_CUDA. */
+#define LC_NOALLOC_MAX_REQUESTS 1024u
+#define LC_NOALLOC_MAX_PARTS 240000u
+lc_status lc_run_batch_noalloc(const lc_req* reqs, size_t count, int32_t* status_dev, lc_mode m,
+                               void* stream);
+
 /* Seeded input generator (not part of the paper's method): writes bytes
  * [offset, offset + n) of the counter-based SplitMix64 byte stream `seed`
  * (Steele, Lea & Flood 2014; byte j = byte j mod 8, little-endian, of word

@@ -445,6 +445,14 @@ lc_status ensure_status_tmp(lc_ctx* ctx, size_t count) {
 
 }  // namespace
 
+namespace lc {
+// Request validation and framing lengths, shared with other entry points.
+int32_t validate_request(const lc_params& p, const lc_req& r, lc_mode m, size_t* n) {
+  return validate_req(p, r, m, n);
+}
+size_t parts_of(const lc_params& p, size_t n, lc_mode m) { return nblocks_of(p, n, m); }
+}  // namespace lc
+
 // ===========================================================================
 // Public ABI
 // ===========================================================================

@@ -124,6 +124,8 @@ _SIGNATURES = {
     "lc_plan_batch": (C.c_int, [C.POINTER(lc_params), C.POINTER(lc_req), C.c_size_t, C.c_int,
                                 C.c_void_p, C.POINTER(C.c_uint64)]),
     "lc_probe_pipes": (C.c_int, [C.c_int, C.POINTER(lc_pipe_rates)]),
+    "lc_run_batch_noalloc": (C.c_int, [C.POINTER(lc_req), C.c_size_t, C.c_void_p, C.c_int,
+                                       C.c_void_p]),
     "lc_synth_uniform": (C.c_int, [C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint64, C.c_void_p]),
 }
 
@@ -309,6 +311,11 @@ class Batch:
 
 def lc_run_batch(ctx, batch: Batch, status_dev, mode=LC_PARALLEL, stream=None) -> int:
     return load().lc_run_batch(ctx, batch.reqs, batch.count, _ptr(status_dev), mode, _stream(stream))
+
+
+def lc_run_batch_noalloc(batch: Batch, status_dev, mode=LC_PARALLEL, stream=None) -> int:
+    return load().lc_run_batch_noalloc(batch.reqs, batch.count, _ptr(status_dev), mode,
+                                       _stream(stream))
 
 
 def lc_run_batch_host(ctx, batch: Batch, status_host, mode=LC_PARALLEL, stream=None) -> int:
