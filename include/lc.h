@@ -262,6 +262,30 @@ lc_status lc_probe_pipes(int device, lc_pipe_rates* out);
 lc_status lc_run_batch_noalloc(const lc_req* reqs, size_t count, int32_t* status_dev, lc_mode m,
                                void* stream);
 
+/* Exactness check of the integer-pipe binary64 routines (not part of the
+ * paper's method).  GB300 issues binary64 add/multiply at about 1/38 of its
+ * 32-bit integer rate, so the v1 kernel computes part of its binary64 work
+ * with integer instructions that reproduce IEEE-754 round-to-nearest-even
+ * bit for bit.  This call evaluates routine `op` on n operand bit patterns
+ * (a_dev, and b_dev for the two-operand routines) and writes the routine's
+ * result bits to sw_dev and the hardware instruction's to hw_dev (device
+ * arrays of n uint64).  LC_SFP_FLOOR13 gives the low 32 bits of
+ * floor(RN(a * 10^13)) as cvt.rmi.s64.f64 computes it.  Asynchronous. */
+enum {
+  LC_SFP_ADD = 0,     /* a + b */
+  LC_SFP_SUB = 1,     /* a - b */
+  LC_SFP_MUL = 2,     /* a * b */
+  LC_SFP_MUL10 = 3,   /* 10 * a */
+  LC_SFP_MUL28 = 4,   /* 28 * a */
+  LC_SFP_FLOOR13 = 5  /* low 32 bits of floor(RN(a * 10^13)) */
+};
+lc_status lc_softfp_eval(uint32_t op, const uint64_t* a_dev, const uint64_t* b_dev, uint64_t* sw_dev,
+                         uint64_t* hw_dev, size_t n, void* stream);
+
+/* The binary64 operations the v1 kernel computes on the integer pipe, as a
+ * bit mask fixed at build time (diagnostic). */
+uint32_t lc_emu_mask(void);
+
 /* Seeded input generator (not part of the paper's method): writes bytes
  * [offset, offset + n) of the counter-based SplitMix64 byte stream `seed`
  * (Steele, Lea & Flood 2014; byte j = byte j mod 8, little-endian, of word

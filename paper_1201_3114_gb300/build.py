@@ -28,7 +28,7 @@ NVCC_FLAGS = ARCH + [
     "-Xcompiler", "-Wall",
     "-I", os.path.join(ROOT, "include"),
 ]
-SOURCES = ["cipher.cu", "api.cu", "keysched.cpp", "probe.cu", "noalloc.cu"]
+SOURCES = ["cipher.cu", "api.cu", "keysched.cpp", "probe.cu", "noalloc.cu", "softfp_eval.cu"]
 
 
 def nvcc() -> str:

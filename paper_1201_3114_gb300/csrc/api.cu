@@ -17,13 +17,15 @@
 #include "lc_internal.h"
 
 namespace lc {
-size_t batch_kernel_smem(bool k4);
-const void* batch_kernel_ptr(bool k4);
-cudaError_t launch_batch(bool k4, int grid, int block, const uint8_t* ws, uint32_t* scratch,
+int kernel_variant(const DevParams& p);
+size_t batch_kernel_smem(int variant);
+const void* batch_kernel_ptr(int variant);
+cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
                          const DevParams& p, const double* theta, cudaStream_t s);
 cudaError_t launch_finalize(int grid, const uint8_t* ws, const uint32_t* scratch, uint32_t block_len,
                             cudaStream_t s);
 cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offset, cudaStream_t s);
+uint32_t emu_mask();
 }  // namespace lc
 
 using namespace lc;
@@ -50,7 +52,7 @@ struct lc_ctx {
   int sm_count = 0;
   lc_params params{};
   DevParams dparams{};
-  bool k4 = true;
+  int variant = kVariantV1;
 
   double* theta_dev = nullptr;
   uint8_t* ws_dev = nullptr;  // header | msgs | rows | init status
@@ -223,9 +225,9 @@ lc_status drain_timing(lc_ctx* ctx) {
 
 int resident_ctas(lc_ctx* ctx, int threads) {
   int per_sm = 0;
-  const void* fn = batch_kernel_ptr(ctx->k4);
+  const void* fn = batch_kernel_ptr(ctx->variant);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads,
-                                                    batch_kernel_smem(ctx->k4)) != cudaSuccess ||
+                                                    batch_kernel_smem(ctx->variant)) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return per_sm;
@@ -252,7 +254,7 @@ lc_status build_graph(lc_ctx* ctx) {
   cudaError_t e = cudaMemsetAsync(ctx->scratch_dev, 0, (4 + ctx->fail_cap) * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.a, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
-    e = launch_batch(ctx->k4, ctx->grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams,
+    e = launch_batch(ctx->variant, ctx->grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams,
                      ctx->theta_dev, s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.b, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
@@ -504,7 +506,7 @@ lc_status lc_ctx_create(int device, lc_ctx** out) {
   DeviceGuard g(device);
   lc_params_default(&ctx->params);
   to_dev_params(ctx->params, &ctx->dparams);
-  ctx->k4 = ctx->dparams.k_all4 != 0;
+  ctx->variant = kernel_variant(ctx->dparams);
   lc_status st = LC_OK;
   cudaError_t e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
@@ -515,9 +517,9 @@ lc_status lc_ctx_create(int device, lc_ctx** out) {
     e = cudaMemcpy(ctx->theta_dev, th.data(), kThetaEntries * sizeof(double), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) {
-    for (int k4 = 0; k4 < 2; k4++) {
-      e = cudaFuncSetAttribute(batch_kernel_ptr(k4 != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)batch_kernel_smem(k4 != 0));
+    for (int v = kVariantGeneral; v <= kVariantV1; v++) {
+      e = cudaFuncSetAttribute(batch_kernel_ptr(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)batch_kernel_smem(v));
       if (e != cudaSuccess) break;
     }
   }
@@ -560,7 +562,7 @@ lc_status lc_ctx_set_params(lc_ctx* ctx, const lc_params* p) {
   if (!ctx || !p || !params_valid(*p)) return LC_ERR_ARG;
   ctx->params = *p;
   to_dev_params(*p, &ctx->dparams);
-  ctx->k4 = ctx->dparams.k_all4 != 0;
+  ctx->variant = kernel_variant(ctx->dparams);
   ctx->keys.clear();
   ctx->graph_valid = false;
   return LC_OK;
@@ -804,6 +806,8 @@ lc_status lc_ctx_kernel_time(lc_ctx* ctx, double* total_ms, uint64_t* launches) 
 }
 
 uint64_t lc_ctx_launch_count(const lc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+uint32_t lc_emu_mask(void) { return emu_mask(); }
 
 lc_status lc_key_info(const lc_params* p, const uint8_t* pw, size_t pw_len, lc_key_info_t* out) {
   if (!out) return LC_ERR_ARG;

@@ -5,19 +5,32 @@
 // version (Sec. 5) or the whole message in the sequential version (Sec. 3).
 // Its Lorenz state (x, y, z) stays in registers for the part's lifetime; the
 // part's bytes stream through 16-byte vector loads and stores.  Every
-// floating-point operation is an explicit round-to-nearest binary64
-// intrinsic (__dadd_rn / __dsub_rn / __dmul_rn) and the file is compiled
-// with --fmad=false, so no multiply-add contraction can change a rounding:
-// the results are bit-identical to a plain IEEE-754 evaluation in the
-// paper's operation order.
+// binary64 operation is rounded once, to nearest, exactly as written (the
+// file is compiled with --fmad=false and uses explicit _rn intrinsics or the
+// bit-exact integer versions of softfp64.cuh), so the results are
+// bit-identical to a plain IEEE-754 evaluation in the paper's order.
 //
-// Nothing here is a dense contraction, so no tensor-core path exists: the
-// kernel is bound by the FP64 issue rate of the SM.
+// Nothing here is a dense contraction, so there is no tensor-core path: the
+// kernel is bound by the SM's binary64 issue rate, which on GB300 is about
+// 1/38 of its 32-bit integer rate.  The v1 fast path therefore computes a
+// chosen share of its binary64 operations on the integer pipe.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "lc_internal.h"
+#include "softfp64.cuh"
+
+// Binary64 operations of the v1 fast path computed on the integer pipe
+// (bit mask, see kEmu* below).  Chosen by measurement on GB300.
+#ifndef LC_EMU_MASK
+#define LC_EMU_MASK 0xFFu
+#endif
+// Minimum resident 256-thread CTAs per SM the v1 kernel is compiled for
+// (bounds its registers per thread).  Chosen by measurement on GB300.
+#ifndef LC_MIN_CTAS
+#define LC_MIN_CTAS 3
+#endif
 
 namespace cg = cooperative_groups;
 
@@ -28,12 +41,49 @@ namespace {
 // nu = floor(log10 2^(xi - 6)) = 13 for xi = 52 (Sec. 3.1, Eq. 8).
 constexpr double kScale = 1e13;
 
+enum : uint32_t {
+  kEmuSmallMul = 1u << 0,  // sigma (y - x) and rho x, exact small-integer multiples
+  kEmuFloor = 1u << 1,     // floor(alpha 10^13)
+  kEmuMulDtX = 1u << 2,
+  kEmuMulDtY = 1u << 3,
+  kEmuMulDtZ = 1u << 4,
+  kEmuMulXZ = 1u << 5,
+  kEmuMulXY = 1u << 6,
+  kEmuMulBZ = 1u << 7,
+  kEmuSubYX = 1u << 8,
+  kEmuSubRY = 1u << 9,
+  kEmuSubXZ = 1u << 10,
+  kEmuSubBZ = 1u << 11,
+  kEmuAddX = 1u << 12,
+  kEmuAddY = 1u << 13,
+  kEmuAddZ = 1u << 14,
+  kEmuKick = 1u << 15,
+  kEmuAprime = 1u << 16,
+};
+
+template <bool SW>
+__device__ __forceinline__ double f_add(double a, double b) {
+  return SW ? sfp::dadd(a, b) : __dadd_rn(a, b);
+}
+template <bool SW>
+__device__ __forceinline__ double f_sub(double a, double b) {
+  return SW ? sfp::dsub(a, b) : __dsub_rn(a, b);
+}
+template <bool SW>
+__device__ __forceinline__ double f_mul(double a, double b) {
+  return SW ? sfp::dmul(a, b) : __dmul_rn(a, b);
+}
+
+__device__ __forceinline__ double pick(uint32_t m, double x, double y, double z) {
+  return m == 0 ? x : (m == 1 ? y : z);
+}
+
 // ---------------------------------------------------------------------------
 // Eq. 1 read as forward Euler of the Lorenz system:
 //   x += dt * (sigma (y - x)),  y += dt * ((rho x - y) - x z),
 //   z += dt * (x y - beta z),   each operation rounded once.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void euler_step(double& x, double& y, double& z, const DevParams& p) {
+__device__ __forceinline__ void euler_hw(double& x, double& y, double& z, const DevParams& p) {
   const double dx = __dmul_rn(p.sigma, __dsub_rn(y, x));
   const double dy = __dsub_rn(__dsub_rn(__dmul_rn(p.rho, x), y), __dmul_rn(x, z));
   const double dz = __dsub_rn(__dmul_rn(x, y), __dmul_rn(p.beta, z));
@@ -42,118 +92,193 @@ __device__ __forceinline__ void euler_step(double& x, double& y, double& z, cons
   z = __dadd_rn(z, __dmul_rn(p.dt, dz));
 }
 
-__device__ __forceinline__ double pick(uint32_t m, double x, double y, double z) {
-  return m == 0 ? x : (m == 1 ? y : z);
+// The same step with sigma = 10 = 5 * 2 and rho = 28 = 7 * 4, each
+// operation on the pipe the mask M selects.
+template <uint32_t M>
+__device__ __forceinline__ void euler_v1(double& x, double& y, double& z, double beta, double dt) {
+  const double yx = f_sub<(M & kEmuSubYX) != 0>(y, x);
+  const double dx = (M & kEmuSmallMul) ? sfp::mul_small<5, 1>(yx) : __dmul_rn(10.0, yx);
+  const double rx = (M & kEmuSmallMul) ? sfp::mul_small<7, 2>(x) : __dmul_rn(28.0, x);
+  const double xz = f_mul<(M & kEmuMulXZ) != 0>(x, z);
+  const double dy = f_sub<(M & kEmuSubXZ) != 0>(f_sub<(M & kEmuSubRY) != 0>(rx, y), xz);
+  const double xy = f_mul<(M & kEmuMulXY) != 0>(x, y);
+  const double bz = f_mul<(M & kEmuMulBZ) != 0>(beta, z);
+  const double dz = f_sub<(M & kEmuSubBZ) != 0>(xy, bz);
+  x = f_add<(M & kEmuAddX) != 0>(x, f_mul<(M & kEmuMulDtX) != 0>(dt, dx));
+  y = f_add<(M & kEmuAddY) != 0>(y, f_mul<(M & kEmuMulDtY) != 0>(dt, dy));
+  z = f_add<(M & kEmuAddZ) != 0>(z, f_mul<(M & kEmuMulDtZ) != 0>(dt, dz));
 }
 
 // floor(RN(alpha * 10^13)) as a two's complement int64: cvt.rmi.s64.f64
 // saturates out-of-range values and maps NaN to 0.
-__device__ __forceinline__ uint64_t floor_scaled(double alpha) {
+__device__ __forceinline__ uint64_t floor_scaled_hw(double alpha) {
   return (uint64_t)__double2ll_rd(__dmul_rn(alpha, kScale));
 }
 
-// One trajectory's state between bytes (Sec. 3.2).  V_i caches
-// floor(alpha_i 10^13): alpha_i only changes in Step 3, and every R_nu of
-// the following byte reads the same V_i.
-struct Traj {
-  double x, y, z;
-  double ax, ay, az;  // a'
+// ---------------------------------------------------------------------------
+// Trajectory state between bytes (Sec. 3.2).  V_i caches floor(alpha_i
+// 10^13): alpha_i only changes in Step 3, and every R_nu of the following
+// byte reads the same V_i.
+// ---------------------------------------------------------------------------
+
+// Any parameters; binary64 on the FP64 pipe.  K4: k = (4, 4, 4).
+template <bool K4>
+struct GeneralPath {
+  double x, y, z, ax, ay, az;
   uint64_t V0, V1, V2;
-  uint32_t mu0, mu1, mu2;
-  uint32_t om0, om1, om2;
+  uint32_t mu0, mu1, mu2, om0, om1, om2;
+
+  static constexpr int kThetaRows = K4 ? 4 : kMaxK;
+  static constexpr int kMinCtas = 1;
+
+  __device__ __forceinline__ void warm(const DevParams& p) {
+    for (uint32_t s = 0; s < p.n_warm; s++) euler_hw(x, y, z, p);
+  }
+  __device__ __forceinline__ void set_alpha() {
+    V0 = floor_scaled_hw(pick(mu0, x, y, z));
+    V1 = floor_scaled_hw(pick(mu1, x, y, z));
+    V2 = floor_scaled_hw(pick(mu2, x, y, z));
+  }
+  __device__ __forceinline__ static uint32_t rb(uint64_t V, uint32_t om) {
+    return (uint32_t)(V >> (8u * om)) & 255u;
+  }
+  __device__ __forceinline__ static uint32_t modk(uint32_t v, uint32_t k) { return K4 ? (v & 3u) : v % k; }
+
+  // Sec. 3.2, Steps 1-3, for one byte.  dec = 0: in is P_i, returns C_i.
+  // dec = 1: in is C_i, returns P_i.  The direction is data, not control
+  // flow, so encrypting and decrypting threads of one warp never diverge.
+  __device__ __forceinline__ uint32_t step(uint32_t in, uint32_t dec, const DevParams& p,
+                                           const double* __restrict__ theta) {
+    // Step 1 (Eqs. 9, 10): R_nu(alpha_1, Omega_1) + R_nu(alpha_2, Omega_2).
+    const uint32_t R1 = rb(V0, om0), R2 = rb(V1, om1);
+    const uint32_t s = R1 + R2;
+    const uint32_t out = (dec ? (in - s) : (in + s)) & 255u;
+    const uint32_t P = dec ? out : in;
+    // Step 2: Theta = P / 10^(3 + Omega_3) kicks r[mu_3], then F.
+    const double kicked = __dadd_rn(pick(mu2, x, y, z), theta[om2 * 256u + P]);
+    x = mu2 == 0 ? kicked : x;
+    y = mu2 == 1 ? kicked : y;
+    z = mu2 == 2 ? kicked : z;
+    for (uint32_t k = 0; k < p.steps_per_byte; k++) euler_hw(x, y, z, p);
+    // Step 3: mu from the old alpha and Omega; alpha re-read from r with the
+    // new mu (Eq. 6); Omega from the new alpha and the old Omega; r += a'.
+    const uint32_t R3 = rb(V2, om2);
+    mu0 = (mu0 + R1) % 3u;
+    mu1 = (mu1 + R2) % 3u;
+    mu2 = (mu2 + R3) % 3u;
+    set_alpha();
+    om0 = modk(om0 + rb(V0, om0), p.k[0]);
+    om1 = modk(om1 + rb(V1, om1), p.k[1]);
+    om2 = modk(om2 + rb(V2, om2), p.k[2]);
+    x = __dadd_rn(x, ax);
+    y = __dadd_rn(y, ay);
+    z = __dadd_rn(z, az);
+    return out;
+  }
 };
 
-__device__ __forceinline__ uint32_t rbyte(uint64_t V, uint32_t om) {
-  return (uint32_t)(V >> (8u * om)) & 255u;
-}
+// sigma = 10, rho = 28, k = (4, 4, 4): the v1 constants.  Only bytes 0-3 of
+// V are ever read, so V keeps its low 32 bits.  When mu_i = mu_j, alpha_i
+// and alpha_j are the same coordinate and V_i = V_j is computed once; after
+// the (mu, Omega) lock that every part reaches within a few dozen bytes this
+// is one conversion per byte instead of three.
+template <uint32_t M>
+struct V1Path {
+  double x, y, z, ax, ay, az;
+  uint32_t V0, V1, V2;
+  uint32_t mu0, mu1, mu2, om0, om1, om2;
 
-template <bool K4>
-__device__ __forceinline__ uint32_t mod_k(uint32_t v, uint32_t k) {
-  if (K4) return v & 3u;
-  return v % k;
-}
+  static constexpr int kThetaRows = 4;
+  static constexpr int kMinCtas = LC_MIN_CTAS;
 
-// Sec. 3.2, Steps 1-3, for one byte.  dec = 0: x is P_i, returns C_i.
-// dec = 1: x is C_i, returns P_i.  The direction is data, not control flow,
-// so encrypting and decrypting threads of one warp never diverge.
-template <bool K4>
-__device__ __forceinline__ uint32_t step_byte(Traj& t, uint32_t x, uint32_t dec, const DevParams& p,
-                                              const double* __restrict__ theta) {
-  // Step 1 (Eqs. 9, 10): R_nu(alpha_1, Omega_1) + R_nu(alpha_2, Omega_2).
-  const uint32_t R1 = rbyte(t.V0, t.om0);
-  const uint32_t R2 = rbyte(t.V1, t.om1);
-  const uint32_t s = R1 + R2;
-  const uint32_t y = (dec ? (x - s) : (x + s)) & 255u;
-  const uint32_t P = dec ? y : x;
+  __device__ __forceinline__ static uint32_t vf(double a) {
+    if (M & kEmuFloor) return sfp::floor_scaled_lo32(a);
+    return (uint32_t)floor_scaled_hw(a);
+  }
+  // The same inside a branch: out of line, so that a skipped conversion does
+  // not issue predicated-off binary64 instructions.
+  __device__ __forceinline__ static uint32_t vf_branch(double a) {
+    if (M & kEmuFloor) return sfp::floor_scaled_lo32(a);
+    return sfp::hw_floor13_lo32(a);
+  }
+  __device__ __forceinline__ void warm(const DevParams& p) {
+    const double beta = p.beta, dt = p.dt;
+    for (uint32_t s = 0; s < p.n_warm; s++) euler_v1<M>(x, y, z, beta, dt);
+  }
+  __device__ __forceinline__ void set_alpha() {
+    V0 = vf(pick(mu0, x, y, z));
+    if (mu1 == mu0) {
+      V1 = V0;
+    } else {
+      V1 = vf_branch(pick(mu1, x, y, z));
+    }
+    if (mu2 == mu0) {
+      V2 = V0;
+    } else if (mu2 == mu1) {
+      V2 = V1;
+    } else {
+      V2 = vf_branch(pick(mu2, x, y, z));
+    }
+  }
+  __device__ __forceinline__ static uint32_t rb(uint32_t V, uint32_t om) { return (V >> (8u * om)) & 255u; }
 
-  // Step 2: Theta = P / 10^(3 + Omega_3) kicks r[mu_3], then F.
-  const double th = theta[t.om2 * 256u + P];
-  const double kicked = __dadd_rn(pick(t.mu2, t.x, t.y, t.z), th);
-  t.x = t.mu2 == 0 ? kicked : t.x;
-  t.y = t.mu2 == 1 ? kicked : t.y;
-  t.z = t.mu2 == 2 ? kicked : t.z;
-  for (uint32_t k = 0; k < p.steps_per_byte; k++) euler_step(t.x, t.y, t.z, p);
-
-  // Step 3: mu from the old alpha and Omega; alpha re-read from r with the
-  // new mu (Eq. 6); Omega from the new alpha and the old Omega; r += a'.
-  const uint32_t R3 = rbyte(t.V2, t.om2);
-  t.mu0 = (t.mu0 + R1) % 3u;
-  t.mu1 = (t.mu1 + R2) % 3u;
-  t.mu2 = (t.mu2 + R3) % 3u;
-  t.V0 = floor_scaled(pick(t.mu0, t.x, t.y, t.z));
-  t.V1 = floor_scaled(pick(t.mu1, t.x, t.y, t.z));
-  t.V2 = floor_scaled(pick(t.mu2, t.x, t.y, t.z));
-  t.om0 = mod_k<K4>(t.om0 + rbyte(t.V0, t.om0), p.k[0]);
-  t.om1 = mod_k<K4>(t.om1 + rbyte(t.V1, t.om1), p.k[1]);
-  t.om2 = mod_k<K4>(t.om2 + rbyte(t.V2, t.om2), p.k[2]);
-  t.x = __dadd_rn(t.x, t.ax);
-  t.y = __dadd_rn(t.y, t.ay);
-  t.z = __dadd_rn(t.z, t.az);
-  return y;
-}
-
-template <bool K4>
-__device__ __forceinline__ uint32_t step_word(Traj& t, uint32_t w, uint32_t dec, const DevParams& p,
-                                              const double* __restrict__ theta) {
-  uint32_t o = 0;
-#pragma unroll
-  for (int j = 0; j < 4; j++) o |= step_byte<K4>(t, (w >> (8 * j)) & 255u, dec, p, theta) << (8 * j);
-  return o;
-}
+  __device__ __forceinline__ uint32_t step(uint32_t in, uint32_t dec, const DevParams& p,
+                                           const double* __restrict__ theta) {
+    const uint32_t R1 = rb(V0, om0), R2 = rb(V1, om1);
+    const uint32_t s = R1 + R2;
+    const uint32_t out = (dec ? (in - s) : (in + s)) & 255u;
+    const uint32_t P = dec ? out : in;
+    const double kicked = f_add<(M & kEmuKick) != 0>(pick(mu2, x, y, z), theta[om2 * 256u + P]);
+    x = mu2 == 0 ? kicked : x;
+    y = mu2 == 1 ? kicked : y;
+    z = mu2 == 2 ? kicked : z;
+    for (uint32_t k = 0; k < p.steps_per_byte; k++) euler_v1<M>(x, y, z, p.beta, p.dt);
+    const uint32_t R3 = rb(V2, om2);
+    mu0 = (mu0 + R1) % 3u;
+    mu1 = (mu1 + R2) % 3u;
+    mu2 = (mu2 + R3) % 3u;
+    set_alpha();
+    om0 = (om0 + rb(V0, om0)) & 3u;
+    om1 = (om1 + rb(V1, om1)) & 3u;
+    om2 = (om2 + rb(V2, om2)) & 3u;
+    x = f_add<(M & kEmuAprime) != 0>(x, ax);
+    y = f_add<(M & kEmuAprime) != 0>(y, ay);
+    z = f_add<(M & kEmuAprime) != 0>(z, az);
+    return out;
+  }
+};
 
 // One trajectory: Eq. 5 plus the part offset b * eta, the warm-up, then the
 // part's body bytes and its tag.  Returns the tag verdict (always true when
 // encrypting).
-template <bool K4>
-__device__ bool run_row(const DevMsg& M, uint32_t b, const DevParams& p,
+template <class Path>
+__device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
                         const double* __restrict__ theta) {
-  const bool seq = (M.flags & kFlagSequential) != 0;
-  const uint32_t dec = (M.flags & kFlagDecrypt) ? 1u : 0u;
+  const bool seq = (Mg.flags & kFlagSequential) != 0;
+  const uint32_t dec = (Mg.flags & kFlagDecrypt) ? 1u : 0u;
   const uint64_t lo = seq ? 0 : (uint64_t)b * p.block_len;
-  const uint64_t len = seq ? M.n : min((uint64_t)p.block_len, M.n - lo);
-  const uint64_t tag_off = M.n + (seq ? 0 : (uint64_t)b * p.tag_len);
+  const uint64_t len = seq ? Mg.n : min((uint64_t)p.block_len, Mg.n - lo);
+  const uint64_t tag_off = Mg.n + (seq ? 0 : (uint64_t)b * p.tag_len);
 
-  Traj t;
+  Path t;
   const double off = __dmul_rn((double)b, p.eta);
-  t.x = __dadd_rn(M.base[0], off);
-  t.y = __dadd_rn(M.base[1], off);
-  t.z = __dadd_rn(M.base[2], off);
-  t.ax = M.aprime[0];
-  t.ay = M.aprime[1];
-  t.az = M.aprime[2];
-  for (uint32_t s = 0; s < p.n_warm; s++) euler_step(t.x, t.y, t.z, p);
-  t.mu0 = M.key_bits & 3u;
-  t.mu1 = (M.key_bits >> 2) & 3u;
-  t.mu2 = (M.key_bits >> 4) & 3u;
-  t.om0 = (M.key_bits >> 8) & 15u;
-  t.om1 = (M.key_bits >> 12) & 15u;
-  t.om2 = (M.key_bits >> 16) & 15u;
-  t.V0 = floor_scaled(pick(t.mu0, t.x, t.y, t.z));
-  t.V1 = floor_scaled(pick(t.mu1, t.x, t.y, t.z));
-  t.V2 = floor_scaled(pick(t.mu2, t.x, t.y, t.z));
+  t.x = __dadd_rn(Mg.base[0], off);
+  t.y = __dadd_rn(Mg.base[1], off);
+  t.z = __dadd_rn(Mg.base[2], off);
+  t.ax = Mg.aprime[0];
+  t.ay = Mg.aprime[1];
+  t.az = Mg.aprime[2];
+  t.warm(p);
+  t.mu0 = Mg.key_bits & 3u;
+  t.mu1 = (Mg.key_bits >> 2) & 3u;
+  t.mu2 = (Mg.key_bits >> 4) & 3u;
+  t.om0 = (Mg.key_bits >> 8) & 15u;
+  t.om1 = (Mg.key_bits >> 12) & 15u;
+  t.om2 = (Mg.key_bits >> 16) & 15u;
+  t.set_alpha();
 
-  const uint8_t* src = M.in + lo;
-  uint8_t* dst = M.out + lo;
+  const uint8_t* src = Mg.in + lo;
+  uint8_t* dst = Mg.out + lo;
   uint64_t i = 0;
   if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
     const uint64_t nv = len >> 4;
@@ -164,28 +289,39 @@ __device__ bool run_row(const DevMsg& M, uint32_t b, const DevParams& p,
       for (uint64_t c = 0; c < nv; c++) {
         uint4 nxt = cur;
         if (c + 1 < nv) nxt = s4[c + 1];  // read ahead before the store (in-place safe)
-        uint4 o;
-        o.x = step_word<K4>(t, cur.x, dec, p, theta);
-        o.y = step_word<K4>(t, cur.y, dec, p, theta);
-        o.z = step_word<K4>(t, cur.z, dec, p, theta);
-        o.w = step_word<K4>(t, cur.w, dec, p, theta);
-        d4[c] = o;
+        // 16 bytes through a rolled loop: the 128-bit input shifts down one
+        // byte per step and each output byte enters at the top.
+        uint32_t i0 = cur.x, i1 = cur.y, i2 = cur.z, i3 = cur.w;
+        uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+#pragma unroll 1
+        for (int j = 0; j < 16; j++) {
+          const uint32_t yb = t.step(i0 & 255u, dec, p, theta);
+          i0 = __funnelshift_r(i0, i1, 8);
+          i1 = __funnelshift_r(i1, i2, 8);
+          i2 = __funnelshift_r(i2, i3, 8);
+          i3 >>= 8;
+          o0 = __funnelshift_r(o0, o1, 8);
+          o1 = __funnelshift_r(o1, o2, 8);
+          o2 = __funnelshift_r(o2, o3, 8);
+          o3 = (o3 >> 8) | (yb << 24);
+        }
+        d4[c] = make_uint4(o0, o1, o2, o3);
         cur = nxt;
       }
     }
     i = nv << 4;
   }
-  for (; i < len; i++) dst[i] = (uint8_t)step_byte<K4>(t, src[i], dec, p, theta);
+  for (; i < len; i++) dst[i] = (uint8_t)t.step(src[i], dec, p, theta);
 
   // Tag: T further bytes whose plaintext is the message length, LE64(n).
   bool ok = true;
   for (uint32_t q = 0; q < p.tag_len; q++) {
-    const uint32_t Q = (uint32_t)(M.n >> (8 * q)) & 255u;
+    const uint32_t Q = (uint32_t)(Mg.n >> (8 * q)) & 255u;
     if (dec) {
-      const uint32_t got = step_byte<K4>(t, M.in[tag_off + q], 1u, p, theta);
+      const uint32_t got = t.step(Mg.in[tag_off + q], 1u, p, theta);
       ok = ok && (got == Q);
     } else {
-      M.out[tag_off + q] = (uint8_t)step_byte<K4>(t, Q, 0u, p, theta);
+      Mg.out[tag_off + q] = (uint8_t)t.step(Q, 0u, p, theta);
     }
   }
   return ok;
@@ -200,13 +336,13 @@ __device__ __forceinline__ void load_msg(DevMsg& m, const DevMsg* src) {
 
 // Persistent batched kernel: CTAs stay resident and pull rows of the
 // flattened part table (sorted longest first) with warp-aggregated atomics.
-template <bool K4>
-__global__ void __launch_bounds__(256) batch_kernel(const uint8_t* __restrict__ ws,
+template <class Path>
+__global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_t* __restrict__ ws,
                                                     uint32_t* __restrict__ scratch,
                                                     DevParams p,
                                                     const double* __restrict__ theta_g) {
   extern __shared__ double s_theta[];
-  const int nth = K4 ? 4 * 256 : kThetaEntries;
+  const int nth = Path::kThetaRows * 256;
   for (int i = threadIdx.x; i < nth; i += blockDim.x) s_theta[i] = theta_g[i];
   __syncthreads();
 
@@ -228,7 +364,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const uint8_t* __restrict__ 
     const DevRow row = rows[r];
     DevMsg M;
     load_msg(M, msgs + row.msg);
-    const bool ok = run_row<K4>(M, row.b, p, s_theta);
+    const bool ok = run_row<Path>(M, row.b, p, s_theta);
     if (M.flags & kFlagDecrypt) {
       // Segmented vote: threads of the warp holding parts of the same
       // message combine their verdicts; one atomic per message and warp.
@@ -296,26 +432,42 @@ __global__ void synth_kernel(uint8_t* __restrict__ dst, uint64_t n, uint64_t see
   }
 }
 
+using KGeneral = GeneralPath<false>;
+using KGeneral4 = GeneralPath<true>;
+using KV1 = V1Path<LC_EMU_MASK>;
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Host-side launch helpers (called from api.cu)
+// Host-side launch helpers (called from api.cu and noalloc.cu)
 // ---------------------------------------------------------------------------
 
-size_t batch_kernel_smem(bool k4) { return (k4 ? 4 * 256 : kThetaEntries) * sizeof(double); }
-
-const void* batch_kernel_ptr(bool k4) {
-  return k4 ? reinterpret_cast<const void*>(&batch_kernel<true>)
-            : reinterpret_cast<const void*>(&batch_kernel<false>);
+int kernel_variant(const DevParams& p) {
+  if (!p.k_all4) return kVariantGeneral;
+  if (p.sigma == 10.0 && p.rho == 28.0) return kVariantV1;
+  return kVariantGeneral4;
 }
 
-cudaError_t launch_batch(bool k4, int grid, int block, const uint8_t* ws, uint32_t* scratch,
+size_t batch_kernel_smem(int variant) {
+  return (variant == kVariantGeneral ? kThetaEntries : 4 * 256) * sizeof(double);
+}
+
+const void* batch_kernel_ptr(int variant) {
+  switch (variant) {
+    case kVariantGeneral: return reinterpret_cast<const void*>(&batch_kernel<KGeneral>);
+    case kVariantGeneral4: return reinterpret_cast<const void*>(&batch_kernel<KGeneral4>);
+    default: return reinterpret_cast<const void*>(&batch_kernel<KV1>);
+  }
+}
+
+cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
                          const DevParams& p, const double* theta, cudaStream_t s) {
-  const size_t smem = batch_kernel_smem(k4);
-  if (k4)
-    batch_kernel<true><<<grid, block, smem, s>>>(ws, scratch, p, theta);
-  else
-    batch_kernel<false><<<grid, block, smem, s>>>(ws, scratch, p, theta);
+  const size_t smem = batch_kernel_smem(variant);
+  switch (variant) {
+    case kVariantGeneral: batch_kernel<KGeneral><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
+    case kVariantGeneral4: batch_kernel<KGeneral4><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
+    default: batch_kernel<KV1><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
+  }
   return cudaGetLastError();
 }
 
@@ -332,5 +484,7 @@ cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offse
   synth_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, n, seed, offset);
   return cudaGetLastError();
 }
+
+uint32_t emu_mask() { return LC_EMU_MASK; }
 
 }  // namespace lc

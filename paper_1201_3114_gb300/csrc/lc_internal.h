@@ -15,6 +15,13 @@ constexpr int kMaxK = 8;
 // Theta table: Theta[w][P] = P / 10^(3 + w), w < kMaxK, P < 256 (Sec. 3.2 Step 2).
 constexpr int kThetaEntries = kMaxK * 256;
 
+// Cipher kernel variants: any parameters (FP64 pipe only), any parameters
+// with k = (4, 4, 4), and the v1 constants sigma = 10, rho = 28, k = 4 whose
+// binary64 work is split between the FP64 and integer pipes.
+constexpr int kVariantGeneral = 0;
+constexpr int kVariantGeneral4 = 1;
+constexpr int kVariantV1 = 2;
+
 // Constants of the method as the kernels read them.
 struct DevParams {
   double sigma, rho, beta, dt, eta;

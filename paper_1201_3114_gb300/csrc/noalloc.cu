@@ -18,12 +18,12 @@
 #include "lc_internal.h"
 
 namespace lc {
-cudaError_t launch_batch(bool k4, int grid, int block, const uint8_t* ws, uint32_t* scratch,
+cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
                          const DevParams& p, const double* theta, cudaStream_t s);
 cudaError_t launch_finalize(int grid, const uint8_t* ws, const uint32_t* scratch, uint32_t block_len,
                             cudaStream_t s);
-const void* batch_kernel_ptr(bool k4);
-size_t batch_kernel_smem(bool k4);
+const void* batch_kernel_ptr(int variant);
+size_t batch_kernel_smem(int variant);
 int32_t validate_request(const lc_params& p, const lc_req& r, lc_mode m, size_t* n);
 size_t parts_of(const lc_params& p, size_t n, lc_mode m);
 }  // namespace lc
@@ -190,11 +190,11 @@ extern "C" lc_status lc_run_batch_noalloc(const lc_req* reqs, size_t count, int3
   if (cudaMemsetAsync(flags, 0, (4 + count) * sizeof(uint32_t), s) != cudaSuccess) return LC_ERR_CUDA;
   int sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LC_ERR_CUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_ptr(true), 256,
-                                                    batch_kernel_smem(true)) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_ptr(kVariantV1), 256,
+                                                    batch_kernel_smem(kVariantV1)) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  if (launch_batch(true, sms * per_sm, 256, ws, flags, dp, theta, s) != cudaSuccess) return LC_ERR_CUDA;
+  if (launch_batch(kVariantV1, sms * per_sm, 256, ws, flags, dp, theta, s) != cudaSuccess) return LC_ERR_CUDA;
   if (launch_finalize(256, ws, flags, p.block_len, s) != cudaSuccess) return LC_ERR_CUDA;
   return LC_OK;
 }

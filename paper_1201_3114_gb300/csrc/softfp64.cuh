@@ -1,0 +1,197 @@
+// softfp64.cuh -- IEEE-754 binary64 round-to-nearest-even arithmetic on the
+// 32-bit integer pipe.
+//
+// GB300 executes binary64 add/multiply at about 1/38 of its 32-bit integer
+// rate.  These functions compute the correctly rounded binary64 result of
+// an operation from the operands' bit patterns with integer instructions
+// only, so a kernel can split its binary64 work between the two pipes.  Each
+// function handles the common case (normal operands, normal result) in
+// integer arithmetic and defers every other case (zeros, subnormals,
+// infinities, NaNs, results near overflow or underflow) to the hardware
+// instruction, so the result is bit-identical to the hardware's for every
+// input.  The rounding rule is the textbook one (IEEE 754-2019 Sec. 4.3.1):
+// keep the leading 53 bits, round up when the discarded part exceeds half an
+// ulp, or equals half an ulp and the kept part is odd.
+//
+// Representation: x = (-1)^s * M * 2^(e - 1075) for a normal x, with the
+// biased exponent e in [1, 2046] and the 53-bit significand M in
+// [2^52, 2^53).  Results are packed as s | (E - 1) << 52 + q with q in
+// [2^52, 2^53]: the hidden bit of q adds one to the exponent field, and a
+// rounding carry to q = 2^53 adds one more, which is exactly the binade step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lc {
+namespace sfp {
+
+constexpr uint64_t kSign = 0x8000000000000000ull;
+constexpr uint64_t kFrac = 0x000FFFFFFFFFFFFFull;
+constexpr uint64_t kHidden = 0x0010000000000000ull;
+
+__device__ __forceinline__ uint64_t bits(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ double from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ uint32_t bexp(uint64_t b) { return (uint32_t)(b >> 52) & 0x7FFu; }
+
+// Hardware fallbacks, kept out of line on purpose: a short inline branch is
+// turned into predicated instructions, and a predicated-off binary64
+// instruction still occupies the narrow FP64 pipe.  Behind a call it runs
+// only when the rare case really happens.
+static __device__ __noinline__ double hw_mul(double a, double b) { return __dmul_rn(a, b); }
+static __device__ __noinline__ double hw_add(double a, double b) { return __dadd_rn(a, b); }
+static __device__ __noinline__ uint32_t hw_floor13_lo32(double a) {
+  return (uint32_t)(uint64_t)__double2ll_rd(__dmul_rn(a, 1e13));
+}
+
+__device__ __forceinline__ uint32_t lo32(double x) { return (uint32_t)__double2loint(x); }
+__device__ __forceinline__ uint32_t hi32(double x) { return (uint32_t)__double2hiint(x); }
+__device__ __forceinline__ double pack(uint32_t hi, uint32_t lo) { return __hiloint2double((int)hi, (int)lo); }
+
+// x * (K * 2^E) for a small odd integer K (3 <= K < 256): the product M * K
+// has at most 61 bits and is rounded to 53 by one shift.
+template <uint32_t K, int E>
+__device__ __forceinline__ double mul_small(double x) {
+  static_assert(K >= 3 && K < 256 && (K & 1u), "K must be a small odd integer");
+  constexpr uint32_t kb = (K < 4) ? 2 : (K < 8) ? 3 : (K < 16) ? 4 : (K < 32) ? 5 : (K < 64) ? 6 : (K < 128) ? 7 : 8;
+  const uint32_t xl = lo32(x), xh = hi32(x);
+  const uint32_t e = (xh >> 20) & 0x7FFu;
+  // fast path: normal x and a normal result (margin for the binade step)
+  if (e - 1u >= 2045u - (uint32_t)E - kb) return hw_mul(x, (double)K * (double)(1ll << E));
+  const uint32_t m1 = (xh & 0xFFFFFu) | 0x100000u;
+  const uint64_t plo = (uint64_t)xl * K;                 // m0 K
+  const uint32_t p0 = (uint32_t)plo;
+  const uint32_t p1 = m1 * K + (uint32_t)(plo >> 32);   // P = p1:p0 < 2^61
+  // P has 52 + kb or 53 + kb bits; shift so that 53 remain.
+  const uint32_t sh = kb - 1u + ((p1 >> (20u + kb)) & 1u);
+  uint32_t q0 = __funnelshift_r(p0, p1, sh);
+  uint32_t q1 = p1 >> sh;
+  const uint32_t rem = p0 & ((1u << sh) - 1u);
+  const uint32_t half = 1u << (sh - 1u);
+  const uint32_t up = (rem > half || (rem == half && (q0 & 1u))) ? 1u : 0u;
+  q0 += up;
+  q1 += (q0 < up) ? 1u : 0u;
+  // biased exponent of the result: e + E + sh; the hidden bit of q adds one
+  const uint32_t hi = (xh & 0x80000000u) + ((e + (uint32_t)E + sh - 1u) << 20) + q1;
+  return pack(hi, q0);
+}
+
+// Low 32 bits of floor(RN(a * 10^13)) as a two's complement integer, the
+// value cvt.rmi.s64.f64 gives (saturating, NaN -> 0).  10^13 = 5^13 * 2^13
+// and 5^13 = 1220703125 < 2^31, so M * 5^13 has 83 or 84 bits; rounding it
+// to 53 bits is the binary64 product, and the floor then drops the bits
+// below the binary point.
+__device__ __forceinline__ uint32_t floor_scaled_lo32(double a) {
+  constexpr uint32_t kFive13 = 1220703125u;
+  const uint32_t xl = lo32(a), xh = hi32(a);
+  const uint32_t e = (xh >> 20) & 0x7FFu;
+  // 2^-43 <= |a| < 2^36; the value's own range is checked after rounding
+  if (e - 980u > 78u) return hw_floor13_lo32(a);
+  const uint32_t m1 = (xh & 0xFFFFFu) | 0x100000u;
+  const uint64_t p0 = (uint64_t)xl * kFive13;                       // < 2^63
+  const uint64_t mid = (uint64_t)m1 * kFive13 + (p0 >> 32);         // < 2^53
+  // P = mid:w0 (84 bits): w1 = low(mid), w2 = high(mid)
+  const uint32_t w0 = (uint32_t)p0, w1 = (uint32_t)mid, w2 = (uint32_t)(mid >> 32);
+  const uint32_t top = (w2 >> 19) & 1u;  // P >= 2^83
+  const uint32_t sh = 30u + top;         // q = P >> sh has 53 bits
+  uint32_t q0 = __funnelshift_r(w0, w1, sh);
+  uint32_t q1 = __funnelshift_r(w1, w2, sh);
+  const uint32_t rem = w0 & ((1u << sh) - 1u);
+  const uint32_t half = 1u << (sh - 1u);
+  const uint32_t up = (rem > half || (rem == half && (q0 & 1u))) ? 1u : 0u;
+  q0 += up;
+  q1 += (q0 < up) ? 1u : 0u;
+  // RN(a 1e13) = q 2^-d with d = 1062 - e - sh fraction bits
+  const uint32_t d = 1062u - e - sh;
+  if (d - 1u > 52u) return hw_floor13_lo32(a);  // d outside [1, 53]
+  // integer part (low 32 bits) and whether a fraction remains
+  uint32_t ip, frac;
+  if (d < 32u) {
+    ip = __funnelshift_r(q0, q1, d);
+    frac = q0 << (32u - d);
+  } else {
+    ip = q1 >> (d - 32u);
+    frac = q0 | (d > 32u ? (q1 << (64u - d)) : 0u);
+  }
+  if (xh & 0x80000000u) return 0u - ip - (frac != 0u ? 1u : 0u);
+  return ip;
+}
+
+// RN(a * b) for two normal operands with a normal result.
+__device__ __forceinline__ double dmul(double a, double b) {
+  const uint32_t xl = lo32(a), xh = hi32(a), yl = lo32(b), yh = hi32(b);
+  const uint32_t ea = (xh >> 20) & 0x7FFu, eb = (yh >> 20) & 0x7FFu;
+  const uint32_t er = ea + eb - 1023u;  // biased exponent if the product stays in [1, 2)
+  if (ea - 1u >= 2046u || eb - 1u >= 2046u || er - 1u >= 2044u) return hw_mul(a, b);
+  const uint32_t a1 = (xh & 0xFFFFFu) | 0x100000u, b1 = (yh & 0xFFFFFu) | 0x100000u;
+  const uint64_t p00 = (uint64_t)xl * yl;
+  const uint64_t mid = (uint64_t)xl * b1 + (uint64_t)a1 * yl;  // < 2^54
+  const uint64_t p11 = (uint64_t)a1 * b1;                      // < 2^42
+  // P = p00 + mid 2^32 + p11 2^64 = w3:w2:w1:w0, in [2^104, 2^106)
+  const uint64_t s1 = (p00 >> 32) + (uint32_t)mid;
+  const uint64_t s2 = (s1 >> 32) + (mid >> 32) + p11;
+  const uint32_t w0 = (uint32_t)p00, w1 = (uint32_t)s1;
+  const uint32_t w2 = (uint32_t)s2, w3 = (uint32_t)(s2 >> 32);
+  const uint32_t top = (w3 >> 9) & 1u;  // P >= 2^105
+  const uint32_t s = 20u + top;         // drop 52 + top bits: w0 and s bits of w1
+  uint32_t q0 = __funnelshift_r(w1, w2, s);
+  uint32_t q1 = __funnelshift_r(w2, w3, s);
+  const uint32_t guard = (w1 >> (s - 1u)) & 1u;
+  const uint32_t sticky = w0 | (w1 << (33u - s));
+  const uint32_t up = guard & ((sticky != 0u) | (q0 & 1u));
+  q0 += up;
+  q1 += (q0 < up) ? 1u : 0u;
+  const uint32_t hi = ((xh ^ yh) & 0x80000000u) + ((er + top - 1u) << 20) + q1;
+  return pack(hi, q0);
+}
+
+// RN(a + b) for two normal operands (either sign) with a normal result.
+// Subtraction of operands whose exponents differ by at most one can cancel
+// many leading bits; that case is rare in the cipher and goes to the
+// hardware.  Otherwise the sum needs at most a one-bit renormalisation, and
+// three extra bits (guard, round, sticky) give the correctly rounded result.
+__device__ __forceinline__ double dadd(double a, double b) {
+  uint32_t xh = hi32(a), xl = lo32(a), yh = hi32(b), yl = lo32(b);
+  // order by magnitude: |x| >= |y|
+  const uint32_t mxh = xh & 0x7FFFFFFFu, myh = yh & 0x7FFFFFFFu;
+  const bool swap = (mxh < myh) || (mxh == myh && xl < yl);
+  const uint32_t th = swap ? yh : xh, tl = swap ? yl : xl;
+  yh = swap ? xh : yh;
+  yl = swap ? xl : yl;
+  xh = th;
+  xl = tl;
+  const uint32_t ex = (xh >> 20) & 0x7FFu, ey = (yh >> 20) & 0x7FFu;
+  const uint32_t d = ex - ey;
+  const bool sub = ((xh ^ yh) & 0x80000000u) != 0u;
+  if (ey == 0u || ex - 60u > 1985u || (sub && d <= 1u)) return hw_add(a, b);
+  // significands with three extra low bits: [2^55, 2^56)
+  const uint64_t Mx = (((uint64_t)((xh & 0xFFFFFu) | 0x100000u) << 32) | xl) << 3;
+  const uint64_t My0 = (((uint64_t)((yh & 0xFFFFFu) | 0x100000u) << 32) | yl) << 3;
+  // align: My >> d, the bits shifted out folded into a sticky bit
+  const uint32_t dc = d < 63u ? d : 63u;
+  uint64_t My = My0 >> dc;
+  My |= ((My0 << (63u - dc)) << 1) != 0ull ? 1ull : 0ull;
+  uint64_t R;
+  uint32_t E = ex;
+  if (!sub) {
+    R = Mx + My;  // < 2^57
+    const uint32_t c = (uint32_t)(R >> 56);
+    R = c ? ((R >> 1) | (R & 1ull)) : R;
+    E += c;
+  } else {
+    R = Mx - My;  // in [2^54, 2^56) since d >= 2
+    const uint32_t n = 1u - (uint32_t)((R >> 55) & 1ull);
+    R <<= n;
+    E -= n;
+  }
+  // R in [2^55, 2^56): 53 bits and 3 guard/round/sticky bits
+  uint64_t q = R >> 3;
+  const uint32_t g = (uint32_t)R & 7u;
+  q += (g > 4u || (g == 4u && (q & 1ull))) ? 1ull : 0ull;
+  return from_bits(((uint64_t)(xh & 0x80000000u) << 32) | ((((uint64_t)E - 1ull) << 52) + q));
+}
+
+__device__ __forceinline__ double dsub(double a, double b) { return dadd(a, -b); }
+
+}  // namespace sfp
+}  // namespace lc

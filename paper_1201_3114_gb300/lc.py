@@ -126,6 +126,9 @@ _SIGNATURES = {
     "lc_probe_pipes": (C.c_int, [C.c_int, C.POINTER(lc_pipe_rates)]),
     "lc_run_batch_noalloc": (C.c_int, [C.POINTER(lc_req), C.c_size_t, C.c_void_p, C.c_int,
                                        C.c_void_p]),
+    "lc_softfp_eval": (C.c_int, [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_size_t, C.c_void_p]),
+    "lc_emu_mask": (C.c_uint32, []),
     "lc_synth_uniform": (C.c_int, [C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint64, C.c_void_p]),
 }
 
@@ -143,7 +146,7 @@ def load():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = os.environ.get("LC_LIBRARY") or _build.build()
             if not os.path.exists(path):
                 raise RuntimeError("liblorenzcipher.so is missing at %s" % path)
             lib = C.CDLL(path)
@@ -375,6 +378,18 @@ def lc_probe_pipes(device: int = 0) -> lc_pipe_rates:
     r = lc_pipe_rates()
     check(load().lc_probe_pipes(device, C.byref(r)), "lc_probe_pipes")
     return r
+
+
+LC_SFP_ADD, LC_SFP_SUB, LC_SFP_MUL, LC_SFP_MUL10, LC_SFP_MUL28, LC_SFP_FLOOR13 = range(6)
+
+
+def lc_softfp_eval(op, a_dev, b_dev, sw_dev, hw_dev, n, stream=None) -> int:
+    return load().lc_softfp_eval(op, _ptr(a_dev), _ptr(b_dev), _ptr(sw_dev), _ptr(hw_dev), n,
+                                 _stream(stream))
+
+
+def lc_emu_mask() -> int:
+    return load().lc_emu_mask()
 
 
 def lc_synth_uniform(dst, n, seed, offset=0, stream=None) -> int:
