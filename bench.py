@@ -300,6 +300,34 @@ def reference_arm(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def run_serving(seconds, rate, device, capacity_gbps):
+    """The served configuration (Poisson arrivals, log-uniform 256 B - 16 MiB,
+    50/50, 2 % tampered decrypts, 48 GiB admission budget) for `seconds` of
+    arrivals, then a supplementary run at 0.8x the measured batched
+    capacity, labelled as such."""
+    from paper_1201_3114_gb300 import serve, synth
+    srv = serve.Server(device, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30)
+    out = {}
+    try:
+        for label, r in (("offered", rate), ("at_0.8x_capacity", None)):
+            if r is None:
+                mean = 1.5e6
+                r = 0.8 * capacity_gbps * 1e9 / mean
+            w = serve.Workload(synth.cfg5_spec(rate=r, duration=seconds))
+            st = srv.run(w)
+            keep = ("requests", "completed", "p50_ms", "p99_ms", "mean_ms", "served_GBps",
+                    "offered_GBps", "duration_s", "wall_s", "batches", "gpu_launches", "tampered",
+                    "tampered_rejected", "untampered_decrypts", "untampered_decrypts_ok",
+                    "encrypts_ok", "plaintext_checked", "plaintext_mismatches")
+            rec = {k: st[k] for k in keep}
+            rec["rate_req_per_s"] = r
+            rec["served_over_per_message"] = None
+            out[label] = rec
+    finally:
+        srv.close()
+    return out
+
+
 def profile_case(args):
     """One message of args.profile_case MiB, parallel-mode encryption per step."""
     import torch
@@ -344,6 +372,9 @@ def main():
     ap.add_argument("--ref-sample-mb", type=int, default=96)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="length of the served-workload run (0 = skip); 60 is the full config")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--profile-case", type=int, default=0, metavar="MIB",
                     help="only time one MIB-MiB parallel-mode encryption per step (a small "
                          "case for ncu captures); prints a short JSON line")
@@ -532,6 +563,13 @@ def main():
                "call": "lc_run_batch_host"}
         del hin, hout
 
+    # ---- served workload (continuous batching), rank 0
+    served = None
+    if rank == 0 and args.serve_seconds > 0:
+        del Parena, Carena, Oarena
+        torch.cuda.empty_cache()
+        served = run_serving(args.serve_seconds, args.serve_rate, local, value / ws)
+
     # ---- CPU oracle baseline
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample_mb:
@@ -542,6 +580,9 @@ def main():
                "sample": "%.0f MiB: the first parts of every message in proportion to its size"
                          % (b_cpu / 2 ** 20)}
 
+    if served and pm:
+        for rec in served.values():
+            rec["served_over_per_message"] = rec["served_GBps"] / pm["value"]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -555,7 +596,7 @@ def main():
                                   "ctas_per_sm": launch.ctas_per_sm},
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "per_message_launch": pm, "clocks": clk,
+            "per_message_launch": pm, "served": served, "clocks": clk,
             "pipes_probe_gops": {k: round(v, 1) for k, v in pipes.as_dict().items()},
         }
         print(json.dumps(line), flush=True)

@@ -1,0 +1,371 @@
+"""Request serving with continuous batching over the batched cipher path.
+
+Requests (encrypt or decrypt, any size, each with its own password) arrive
+over time.  The loop admits them as device memory frees up, launches the
+admitted ones as one lc_run_batch on a free stream, and records each
+request's latency from arrival to GPU completion.  Every stream has its own
+lc_ctx, so several batches are in flight at once.  When one batch's part
+queue drains, its CTAs retire and the next batch's CTAs take the freed SMs:
+requests that arrived while others were on the GPU overlap with them on the
+device.  Admission is by a device-memory budget, an arena of that many bytes
+carved into power-of-two blocks.  The batched path never changes the
+arithmetic: a request gives the same bytes alone and in any mix.
+
+Payloads live on the device: an encryption reads a slice of a
+device-resident random pool, and a decryption replays the ciphertext of an
+earlier completed encryption (a fraction with one byte flipped, which must
+be rejected).  The host loop handles the bookkeeping only: all cipher work
+runs in the library's kernels.
+"""
+import collections
+import ctypes as C
+import math
+import time
+
+import numpy as np
+
+from . import lc, synth
+
+REQ_DTYPE = np.dtype([("pw", "<u8"), ("pw_len", "<u4"), ("dir", "<u4"), ("inp", "<u8"),
+                      ("in_len", "<u8"), ("out", "<u8"), ("out_cap", "<u8")])
+assert REQ_DTYPE.itemsize == C.sizeof(lc.lc_req)
+
+B = 4096
+T = 8
+
+
+def ct_len(n):
+    return n + T * max(1, -(-n // B))
+
+
+class Arena:
+    """A device byte arena managed as a buddy system: blocks of 2^k bytes
+    (4 KiB up to MAX_CLASS), split on allocation and merged with their free
+    buddy on release, so no size mix strands memory.  Its size is the
+    admission budget."""
+
+    MIN_CLASS = 12
+    MAX_CLASS = 26  # 64 MiB top blocks
+
+    def __init__(self, nbytes, device):
+        import torch
+        top = 1 << self.MAX_CLASS
+        nbytes = max(top, nbytes // top * top)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)  # cpu in host tests
+        self.base = self.buf.data_ptr()
+        self.cap = nbytes
+        self.free = {k: set() for k in range(self.MIN_CLASS, self.MAX_CLASS + 1)}
+        self.free[self.MAX_CLASS] = set(range(0, nbytes, top))
+        self.in_use = 0
+        self.peak = 0
+
+    def alloc(self, n):
+        k = max(self.MIN_CLASS, (max(1, n) - 1).bit_length())
+        if k > self.MAX_CLASS:
+            raise ValueError("request of %d bytes exceeds the largest arena block" % n)
+        j = k
+        while j <= self.MAX_CLASS and not self.free[j]:
+            j += 1
+        if j > self.MAX_CLASS:
+            return None
+        off = self.free[j].pop()
+        while j > k:  # split, keeping the lower half
+            j -= 1
+            self.free[j].add(off + (1 << j))
+        self.in_use += 1 << k
+        self.peak = max(self.peak, self.in_use)
+        return off, k
+
+    def release(self, blk):
+        off, k = blk
+        self.in_use -= 1 << k
+        while k < self.MAX_CLASS:
+            buddy = off ^ (1 << k)
+            if buddy not in self.free[k]:
+                break
+            self.free[k].remove(buddy)
+            off = min(off, buddy)
+            k += 1
+        self.free[k].add(off)
+
+    def view(self, blk, n):
+        return self.buf[blk[0]:blk[0] + n]
+
+
+class Workload:
+    """Served workload: arrival times, sizes, directions, tamper flags and
+    passwords of every request (synth.cfg5_spec by default)."""
+
+    def __init__(self, spec):
+        self.t = np.asarray(spec["t"], dtype=np.float64)
+        self.size = np.asarray(spec["sizes"], dtype=np.int64)
+        self.kind = np.asarray(spec["kind"], dtype=np.int8)
+        self.tamper = np.asarray(spec["tamper"], dtype=bool)
+        self.data_seed = np.asarray(spec["data_seed"], dtype=np.uint64)
+        self.flip_pos = np.asarray(spec["flip_pos"], dtype=np.uint64)
+        self.pw_chars, self.pw_len = synth.passwords_bulk(spec["pw_seed"])
+        self.pw_chars = np.ascontiguousarray(self.pw_chars)
+        self.n = self.t.size
+
+    def pw(self, i):
+        return bytes(self.pw_chars[i, :self.pw_len[i]])
+
+
+class Server:
+    """Continuous-batching request loop over ``streams`` CUDA streams."""
+
+    def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
+                 max_batch_bytes=1 << 30, max_batch_requests=8192, replay_cap_bytes=None,
+                 seed=0x5E4E):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.ctxs = [lc.Context(device) for _ in range(streams)]
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.arena = Arena(budget_bytes, self.device)
+        self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
+        lc.check(lc.lc_synth_uniform(self.pool, pool_bytes, seed, 0, self.streams[0]))
+        self.max_batch_bytes = max_batch_bytes
+        self.max_batch_requests = max_batch_requests
+        self.replay_cap = replay_cap_bytes if replay_cap_bytes is not None else budget_bytes // 4
+        self.status_dev = [torch.zeros(max_batch_requests, dtype=torch.int32, device=self.device)
+                           for _ in range(streams)]
+        self.status_host = [torch.zeros(max_batch_requests, dtype=torch.int32).pin_memory()
+                            for _ in range(streams)]
+        self.reqs = [np.zeros(max_batch_requests, dtype=REQ_DTYPE) for _ in range(streams)]
+        torch.cuda.synchronize()
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+    # ------------------------------------------------------------------
+    def plain_offset(self, w, i, n):
+        """Offset of request i's plaintext in the pool (16-byte aligned)."""
+        span = self.pool.numel() - n
+        return (int(w.data_seed[i]) % max(1, span)) & ~15 if span > 0 else 0
+
+    def run(self, w: Workload, capture=(), verify_every=64, drain_timeout=60.0, poll=0.0002):
+        """Serve every request of ``w``; returns a stats dict.  Requests in
+        ``capture`` keep a host copy of their output (for tests)."""
+        torch = self.torch
+        S = len(self.streams)
+        N = w.n
+        # per-request state
+        status = np.full(N, -1, dtype=np.int32)
+        done_ms = np.full(N, np.nan)
+        n_plain = w.size.copy()          # plaintext length (decrypts: that of the replayed encrypt)
+        src_enc = np.full(N, -1, dtype=np.int64)  # decrypt -> encrypt it replays
+        in_ref = {}                      # decrypt -> replay entry or private tampered copy
+        out_blk = {}                     # request -> arena block of its output
+        captured = {}
+        capture = set(int(c) for c in capture)
+        # Ciphertexts of completed encryptions, newest last: [enc, block, users, evicted].
+        # Decryptions replay the newest one (untampered ones share it read-only;
+        # a tampered one flips a byte in its own copy); the oldest are evicted
+        # above the replay cap and freed when their last user completes.
+        replay = collections.deque()
+        replay_bytes = 0
+        pending = collections.deque()
+        inflight = [None] * S
+        nxt = 0
+        mismatches = 0
+        checked = 0
+        batches = 0
+        launches0 = sum(lc.lc_ctx_launch_count(c.handle) for c in self.ctxs)
+
+        base = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        base.record(self.streams[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        last_arrival = float(w.t[-1]) if N else 0.0
+
+        def unref(entry):
+            entry[2] -= 1
+            if entry[3] and entry[2] == 0:
+                self.arena.release(entry[1])
+
+        def evict():
+            nonlocal replay_bytes
+            while replay_bytes > self.replay_cap and len(replay) > 1:
+                entry = replay.popleft()
+                replay_bytes -= 1 << entry[1][1]
+                entry[3] = True
+                if entry[2] == 0:
+                    self.arena.release(entry[1])
+
+        def complete(s):
+            nonlocal replay_bytes, mismatches, checked
+            rec = inflight[s]
+            idx = rec["idx"]
+            ms = base.elapsed_time(rec["event"])
+            st = self.status_host[s].numpy()[:len(idx)].copy()
+            for k, i in enumerate(idx):
+                status[i] = st[k]
+                done_ms[i] = ms
+                if i in capture:
+                    captured[i] = self.arena.view(out_blk[i], rec["out_len"][k]).cpu().numpy()
+                if w.kind[i] == 0:
+                    blk = out_blk.pop(i)
+                    if st[k] == 0:
+                        replay.append([i, blk, 0, False])
+                        replay_bytes += 1 << blk[1]
+                    else:
+                        self.arena.release(blk)
+                else:
+                    e = src_enc[i]
+                    if st[k] == 0 and (i // 2) % verify_every == 0:
+                        n = int(n_plain[i])
+                        off = self.plain_offset(w, e, n)
+                        checked += 1
+                        if not torch.equal(self.arena.view(out_blk[i], n), self.pool[off:off + n]):
+                            mismatches += 1
+                    self.arena.release(out_blk.pop(i))
+                    ref = in_ref.pop(i)
+                    if isinstance(ref, list):
+                        unref(ref)
+                    else:
+                        self.arena.release(ref)
+            evict()
+            inflight[s] = None
+
+        def form_batch(s):
+            reqs = self.reqs[s]
+            idx, out_len = [], []
+            nbytes = 0
+            scan = len(pending)
+            kept = collections.deque()
+            while pending and scan > 0 and len(idx) < self.max_batch_requests and nbytes < self.max_batch_bytes:
+                scan -= 1
+                i = pending.popleft()
+                k = len(idx)
+                if w.kind[i] == 0:
+                    n = int(w.size[i])
+                    c = ct_len(n)
+                    blk = self.arena.alloc(c)
+                    if blk is None:
+                        kept.append(i)
+                        break
+                    out_blk[i] = blk
+                    src = self.pool.data_ptr() + self.plain_offset(w, i, n)
+                    reqs[k] = (w.pw_chars.ctypes.data + 32 * i, w.pw_len[i], 0, src, n,
+                               self.arena.base + blk[0], c)
+                    out_len.append(c)
+                    nbytes += n
+                else:
+                    if not replay:
+                        kept.append(i)
+                        continue
+                    entry = replay[-1]
+                    e, cblk = entry[0], entry[1]
+                    n = int(w.size[e])
+                    c = ct_len(n)
+                    blk = self.arena.alloc(n)
+                    if blk is None:
+                        kept.append(i)
+                        break
+                    if w.tamper[i]:
+                        own = self.arena.alloc(c)
+                        if own is None:
+                            self.arena.release(blk)
+                            kept.append(i)
+                            break
+                        v = self.arena.view(own, c)
+                        with torch.cuda.stream(self.streams[s]):
+                            v.copy_(self.arena.view(cblk, c))
+                            pos = int(w.flip_pos[i] % np.uint64(c))
+                            v[pos:pos + 1].bitwise_xor_(0x5A)
+                        in_ref[i] = own
+                        src = self.arena.base + own[0]
+                    else:
+                        entry[2] += 1
+                        in_ref[i] = entry
+                        src = self.arena.base + cblk[0]
+                    out_blk[i] = blk
+                    src_enc[i] = e
+                    n_plain[i] = n
+                    reqs[k] = (w.pw_chars.ctypes.data + 32 * e, w.pw_len[e], 1, src, c,
+                               self.arena.base + blk[0], n)
+                    out_len.append(n)
+                    nbytes += n
+                idx.append(i)
+            kept.extend(pending)
+            pending.clear()
+            pending.extend(kept)
+            return idx, out_len
+
+        def launch(s, idx, out_len):
+            nonlocal batches
+            st = self.streams[s]
+            ptr = self.reqs[s].ctypes.data_as(C.POINTER(lc.lc_req))
+            rc = lc.load().lc_run_batch(self.ctxs[s].handle, ptr, len(idx), self.status_dev[s].data_ptr(),
+                                        lc.LC_PARALLEL, st.cuda_stream)
+            lc.check(rc, "lc_run_batch")
+            with torch.cuda.stream(st):
+                self.status_host[s][:len(idx)].copy_(self.status_dev[s][:len(idx)], non_blocking=True)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(st)
+            inflight[s] = {"idx": idx, "out_len": out_len, "event": ev}
+            batches += 1
+
+        while True:
+            now = time.perf_counter() - t0
+            progressed = False
+            j = int(np.searchsorted(w.t, now, side="right"))
+            if j > nxt:
+                pending.extend(range(nxt, j))
+                nxt = j
+                progressed = True
+            for s in range(S):
+                if inflight[s] is not None and inflight[s]["event"].query():
+                    complete(s)
+                    progressed = True
+            for s in range(S):
+                if inflight[s] is None and pending:
+                    idx, out_len = form_batch(s)
+                    if idx:
+                        launch(s, idx, out_len)
+                        progressed = True
+            if nxt >= N and not pending and all(f is None for f in inflight):
+                break
+            if now > last_arrival + drain_timeout:
+                break
+            if not progressed:
+                time.sleep(poll)
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        # release what is still held
+        for entry in replay:
+            entry[3] = True
+            if entry[2] == 0:
+                self.arena.release(entry[1])
+        replay.clear()
+
+        ok = ~np.isnan(done_ms)
+        lat_ms = done_ms[ok] - 1e3 * w.t[ok]
+        served_bytes = int(n_plain[ok].sum())
+        span_s = (np.nanmax(done_ms) / 1e3) if ok.any() else wall
+        tampered = w.tamper & ok
+        untampered_dec = (w.kind == 1) & ~w.tamper & ok
+        return {
+            "requests": int(N), "completed": int(ok.sum()),
+            "p50_ms": float(np.percentile(lat_ms, 50)) if lat_ms.size else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if lat_ms.size else None,
+            "mean_ms": float(lat_ms.mean()) if lat_ms.size else None,
+            "served_GBps": served_bytes / span_s / 1e9,
+            "offered_GBps": float(w.size.sum()) / max(1e-9, float(w.t[-1])) / 1e9 if N else 0.0,
+            "duration_s": float(w.t[-1]) if N else 0.0, "wall_s": wall,
+            "batches": batches,
+            "gpu_launches": sum(lc.lc_ctx_launch_count(c.handle) for c in self.ctxs) - launches0,
+            "tampered": int(tampered.sum()),
+            "tampered_rejected": int((status[tampered] == lc.LC_ERR_INTEGRITY).sum()),
+            "untampered_decrypts": int(untampered_dec.sum()),
+            "untampered_decrypts_ok": int((status[untampered_dec] == 0).sum()),
+            "encrypts_ok": int(((w.kind == 0) & ok & (status == 0)).sum()),
+            "plaintext_checked": checked, "plaintext_mismatches": mismatches,
+            "arena_peak_bytes": self.arena.peak,
+            "status": status, "done_ms": done_ms, "captured": captured,
+            "src_enc": src_enc, "n_plain": n_plain,
+        }

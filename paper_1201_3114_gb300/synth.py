@@ -82,6 +82,22 @@ def password(seed: int, length: int) -> bytes:
     return bytes(int(32 + (int(x) % 95)) for x in w)
 
 
+def passwords_bulk(seeds: np.ndarray, lo: int = 8, hi: int = 32):
+    """Vectorised ``password(s, password_len(s, lo, hi))`` for many seeds:
+    (uint8 array [len(seeds), hi] zero-padded, int64 lengths)."""
+    seeds = np.asarray(seeds, dtype=np.uint64)
+    n = seeds.size
+    with np.errstate(over="ignore"):
+        lw = _mix(seeds + np.uint64(1_000_003 + 1) * GAMMA)
+        lengths = (lo + (lw % np.uint64(hi - lo + 1)).astype(np.int64))
+        j = np.arange(1, hi + 1, dtype=np.uint64)
+        z = seeds[:, None] + j[None, :] * GAMMA
+        chars = (32 + (_mix(z) % np.uint64(95))).astype(np.uint8)
+    mask = np.arange(hi)[None, :] < lengths[:, None]
+    chars[~mask] = 0
+    return chars, lengths
+
+
 def password_len(seed: int, lo: int, hi: int) -> int:
     """A length uniform in [lo, hi]."""
     return lo + word(seed, 1_000_003) % (hi - lo + 1)
