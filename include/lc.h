@@ -286,6 +286,22 @@ lc_status lc_softfp_eval(uint32_t op, const uint64_t* a_dev, const uint64_t* b_d
  * bit mask fixed at build time (diagnostic). */
 uint32_t lc_emu_mask(void);
 
+/* Byte statistics of a device buffer, for the ciphertext analysis of
+ * Sec. 4: the frequency histogram (Fig. 2; the Shannon entropy
+ * S = -sum p_i log2 p_i follows from it) and the sums behind the
+ * auto-correlation of Fig. 3, all exact integers: sum x_i, sum x_i^2 and,
+ * for k = 1..max_lag (max_lag <= LC_STATS_MAX_LAG), sum_{i < n-k} x_i x_{i+k}.
+ * Uses the context's workspace; synchronises `stream`. */
+#define LC_STATS_MAX_LAG 8
+typedef struct {
+  uint64_t n;
+  uint64_t hist[256];
+  uint64_t sum, sum_sq;
+  uint64_t lag_sum[LC_STATS_MAX_LAG];
+} lc_byte_stats_t;
+lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t max_lag,
+                        lc_byte_stats_t* out, void* stream);
+
 /* Seeded input generator (not part of the paper's method): writes bytes
  * [offset, offset + n) of the counter-based SplitMix64 byte stream `seed`
  * (Steele, Lea & Flood 2014; byte j = byte j mod 8, little-endian, of word

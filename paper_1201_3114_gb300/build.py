@@ -28,7 +28,8 @@ NVCC_FLAGS = ARCH + [
     "-Xcompiler", "-Wall",
     "-I", os.path.join(ROOT, "include"),
 ]
-SOURCES = ["cipher.cu", "api.cu", "keysched.cpp", "probe.cu", "noalloc.cu", "softfp_eval.cu"]
+SOURCES = ["cipher.cu", "api.cu", "keysched.cpp", "probe.cu", "noalloc.cu", "softfp_eval.cu",
+           "stats.cu"]
 
 
 def nvcc() -> str:

@@ -26,6 +26,8 @@ cudaError_t launch_finalize(int grid, const uint8_t* ws, const uint32_t* scratch
                             cudaStream_t s);
 cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offset, cudaStream_t s);
 uint32_t emu_mask();
+cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsigned long long* acc,
+                         int sms, cudaStream_t s);
 }  // namespace lc
 
 using namespace lc;
@@ -63,6 +65,7 @@ struct lc_ctx {
   size_t status_tmp_cap = 0;
   uint8_t* io_dev = nullptr;  // staging for lc_run_batch_host
   size_t io_cap = 0;
+  unsigned long long* stats_dev = nullptr;  // lc_byte_stats accumulators
 
   Staging staging[2];
   int slot = 0;
@@ -554,6 +557,7 @@ void lc_ctx_destroy(lc_ctx* ctx) {
   if (ctx->scratch_dev) cudaFree(ctx->scratch_dev);
   if (ctx->status_tmp_dev) cudaFree(ctx->status_tmp_dev);
   if (ctx->io_dev) cudaFree(ctx->io_dev);
+  if (ctx->stats_dev) cudaFree(ctx->stats_dev);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
@@ -808,6 +812,26 @@ lc_status lc_ctx_kernel_time(lc_ctx* ctx, double* total_ms, uint64_t* launches) 
 uint64_t lc_ctx_launch_count(const lc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 uint32_t lc_emu_mask(void) { return emu_mask(); }
+
+lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t max_lag,
+                        lc_byte_stats_t* out, void* stream) {
+  if (!ctx || !out || (n && !data_dev) || max_lag > LC_STATS_MAX_LAG) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  constexpr size_t kWords = 258 + LC_STATS_MAX_LAG;
+  if (!ctx->stats_dev) LC_CUDA(cudaMalloc(&ctx->stats_dev, kWords * sizeof(unsigned long long)));
+  LC_CUDA(launch_stats(data_dev, n, max_lag, ctx->stats_dev, ctx->sm_count, s));
+  unsigned long long acc[kWords];
+  LC_CUDA(cudaMemcpyAsync(acc, ctx->stats_dev, sizeof acc, cudaMemcpyDeviceToHost, s));
+  LC_CUDA(cudaStreamSynchronize(s));
+  out->n = n;
+  for (int b = 0; b < 256; b++) out->hist[b] = acc[b];
+  out->sum = acc[256];
+  out->sum_sq = acc[257];
+  for (int k = 0; k < LC_STATS_MAX_LAG; k++) out->lag_sum[k] = (uint32_t)k < max_lag ? acc[258 + k] : 0;
+  ctx->launches += 1;
+  return LC_OK;
+}
 
 lc_status lc_key_info(const lc_params* p, const uint8_t* pw, size_t pw_len, lc_key_info_t* out) {
   if (!out) return LC_ERR_ARG;

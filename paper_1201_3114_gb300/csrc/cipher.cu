@@ -26,6 +26,11 @@
 #ifndef LC_EMU_MASK
 #define LC_EMU_MASK 0xFFu
 #endif
+// The same for the warm-up steps before the first byte (they carry no
+// per-byte bookkeeping, so their best split can differ).
+#ifndef LC_WARM_MASK
+#define LC_WARM_MASK LC_EMU_MASK
+#endif
 // Minimum resident 256-thread CTAs per SM the v1 kernel is compiled for
 // (bounds its registers per thread).  Chosen by measurement on GB300.
 #ifndef LC_MIN_CTAS
@@ -203,7 +208,7 @@ struct V1Path {
   }
   __device__ __forceinline__ void warm(const DevParams& p) {
     const double beta = p.beta, dt = p.dt;
-    for (uint32_t s = 0; s < p.n_warm; s++) euler_v1<M>(x, y, z, beta, dt);
+    for (uint32_t s = 0; s < p.n_warm; s++) euler_v1<(uint32_t)LC_WARM_MASK>(x, y, z, beta, dt);
   }
   __device__ __forceinline__ void set_alpha() {
     V0 = vf(pick(mu0, x, y, z));

@@ -86,6 +86,19 @@ class lc_pipe_rates(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+LC_STATS_MAX_LAG = 8
+
+
+class lc_byte_stats_t(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint64),
+        ("hist", C.c_uint64 * 256),
+        ("sum", C.c_uint64),
+        ("sum_sq", C.c_uint64),
+        ("lag_sum", C.c_uint64 * LC_STATS_MAX_LAG),
+    ]
+
+
 class LcError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -129,6 +142,8 @@ _SIGNATURES = {
     "lc_softfp_eval": (C.c_int, [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_size_t, C.c_void_p]),
     "lc_emu_mask": (C.c_uint32, []),
+    "lc_byte_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32,
+                                C.POINTER(lc_byte_stats_t), C.c_void_p]),
     "lc_synth_uniform": (C.c_int, [C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint64, C.c_void_p]),
 }
 
@@ -386,6 +401,36 @@ LC_SFP_ADD, LC_SFP_SUB, LC_SFP_MUL, LC_SFP_MUL10, LC_SFP_MUL28, LC_SFP_FLOOR13 =
 def lc_softfp_eval(op, a_dev, b_dev, sw_dev, hw_dev, n, stream=None) -> int:
     return load().lc_softfp_eval(op, _ptr(a_dev), _ptr(b_dev), _ptr(sw_dev), _ptr(hw_dev), n,
                                  _stream(stream))
+
+
+def lc_byte_stats(ctx, data_dev, n, max_lag=LC_STATS_MAX_LAG, stream=None) -> lc_byte_stats_t:
+    out = lc_byte_stats_t()
+    check(load().lc_byte_stats(ctx, _ptr(data_dev), n, max_lag, C.byref(out), _stream(stream)),
+          "lc_byte_stats")
+    return out
+
+
+def entropy_bits(stats: lc_byte_stats_t) -> float:
+    """Shannon entropy (bits per byte) of the histogram (Sec. 4)."""
+    import math
+    n = stats.n
+    return -sum((h / n) * math.log2(h / n) for h in stats.hist if h) if n else 0.0
+
+
+def autocorrelation(stats: lc_byte_stats_t, max_lag=LC_STATS_MAX_LAG):
+    """Lag-k auto-correlation coefficients from the exact sums: the covariance
+    of (x_i, x_{i+k}) over the variance, using the whole-sequence mean."""
+    n = stats.n
+    if n < 2:
+        return [0.0] * max_lag
+    mean = stats.sum / n
+    var = stats.sum_sq / n - mean * mean
+    out = []
+    for k in range(1, max_lag + 1):
+        m = n - k
+        cov = stats.lag_sum[k - 1] / m - mean * mean if m > 0 else 0.0
+        out.append(cov / var if var > 0 else 0.0)
+    return out
 
 
 def lc_emu_mask() -> int:

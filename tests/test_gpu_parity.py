@@ -420,3 +420,20 @@ def test_config4_batch_sampled(ctx):
                 hi = min(n, (b + 1) * B)
                 assert np.array_equal(got[b * B:hi], Cb[b * B:hi]), (m, b)
                 assert np.array_equal(got[n + T * b:n + T * b + T], Cb[n + T * b:n + T * b + T])
+
+
+def test_n_it_steps_per_byte_profile():
+    # The alternative reading of n_it: 3000 Euler steps per byte (Sec. 3.1).
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    po = O.params(steps_per_byte=3000)
+    pl = lc.params(steps_per_byte=3000)
+    with lc.Context(0, pl) as c:
+        for i, n in enumerate([0, 1, 33, 100]):
+            pw = synth.password(synth.subseed(58, i), 8 + i)
+            P = synth.uniform_bytes(synth.subseed(59, i), n)
+            want = O.encrypt(pw, P, O.PARALLEL, po)
+            got = gpu_encrypt(c, pw, P)
+            assert np.array_equal(got, want), n
+            st, back = gpu_decrypt(c, pw, got)
+            assert st == lc.LC_OK and np.array_equal(back, P)

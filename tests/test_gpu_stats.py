@@ -1,0 +1,69 @@
+"""Ciphertext statistics (Sec. 4): the byte-statistics kernel against exact
+numpy sums, and the paper's statistical claims on GPU ciphertexts."""
+import numpy as np
+import pytest
+
+from paper_1201_3114_gb300 import lc, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = lc.Context(0)
+    yield c
+    c.close()
+
+
+def _np_stats(x, max_lag):
+    x = x.astype(np.uint64)
+    hist = np.bincount(x.astype(np.int64), minlength=256)
+    lag = [int((x[:-k] * x[k:]).sum()) if x.size > k else 0 for k in range(1, max_lag + 1)]
+    return hist, int(x.sum()), int((x * x).sum()), lag
+
+
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 100, 65536, 65536 * 3 + 7, 1 << 22])
+def test_stats_exact(ctx, n):
+    x = synth.zipf_text(60 + n % 97, n, zero_run=4096 if n > 8192 else 0)
+    for shift in (0, 3):
+        buf = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+        if n:
+            buf[shift:shift + n] = torch.from_numpy(x).cuda()
+        for max_lag in (0, 1, 8):
+            st = lc.lc_byte_stats(ctx.handle, buf.data_ptr() + shift, n, max_lag)
+            hist, s1, s2, lag = _np_stats(x, max_lag)
+            assert st.n == n
+            assert list(st.hist) == list(hist)
+            assert (st.sum, st.sum_sq) == (s1, s2)
+            assert list(st.lag_sum)[:max_lag] == lag
+
+
+def test_ciphertext_statistics(ctx):
+    # Sec. 4: the ciphertext histogram is flat and carries no correlation
+    # between neighbouring bytes; two close passwords give unrelated
+    # ciphertexts.  Under the Step-3 reading every part reaches the absorbing
+    # (mu, Omega) lock, after which C - P = 2 R is even: the ciphertext's low
+    # bit is the plaintext's.  So for text the entropy is bounded by
+    # 7 + H(low bit of P) (the 7/16 bias of R mod 4 keeps it slightly below),
+    # and for uniform data it is 8.
+    n = 1 << 22
+    P = torch.from_numpy(synth.zipf_text(61, n)).cuda()
+    ps = lc.lc_byte_stats(ctx.handle, P, n)
+    c1 = ctx.encrypt(b"123456", P)
+    c2 = ctx.encrypt(b"123457", P)
+    cs = lc.lc_byte_stats(ctx.handle, c1, n)
+    h = np.array(ps.hist, dtype=np.float64)
+    p1 = h[1::2].sum() / n
+    h_lsb = -(p1 * np.log2(p1) + (1 - p1) * np.log2(1 - p1))
+    assert lc.entropy_bits(ps) < 5.5
+    Hc = lc.entropy_bits(cs)
+    assert 7.95 < Hc <= 7 + h_lsb + 1e-3, (Hc, h_lsb)
+    assert all(abs(r) < 0.01 for r in lc.autocorrelation(cs))
+    assert (c1[:n] != c2[:n]).float().mean().item() > 0.99
+    U = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lc.check(lc.lc_synth_uniform(U, n, 62, 0))
+    cu = lc.lc_byte_stats(ctx.handle, ctx.encrypt(b"uniform", U), n)
+    assert lc.entropy_bits(cu) > 7.999
