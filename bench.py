@@ -353,9 +353,19 @@ def profile_case(args):
     kms, kn = lc.lc_ctx_kernel_time(ctx.handle)
     ops, parts, _ = fp64_ops_per_launch([n])
     ms = e0.elapsed_time(e1) / args.steps
+    # one statistics pass over the ciphertext (outside the timed region)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    st = lc.lc_byte_stats(ctx.handle, Cb, n, 8, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    stats_ms = s0.elapsed_time(s1)
     print(json.dumps({"case": "profile", "mib": args.profile_case, "ms_per_step": ms,
                       "GBps": n / ms / 1e6, "kernel_ms": kms / max(1, kn),
-                      "fp64_gops": ops / (kms / max(1, kn)) / 1e6, "source_hash": source_hash()}))
+                      "fp64_gops": ops / (kms / max(1, kn)) / 1e6, "source_hash": source_hash(),
+                      "stats_ms": stats_ms, "stats_GBps": n / stats_ms / 1e6,
+                      "ciphertext_entropy_bits": lc.entropy_bits(st)}))
     ctx.close()
     return 0
 

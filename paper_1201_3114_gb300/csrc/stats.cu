@@ -4,10 +4,11 @@
 // auto-correlation of Fig. 3.  Every quantity is an exact integer sum, so
 // the result does not depend on the order in which threads add.
 //
-// One pass over the data: HBM-bound.  Each CTA keeps a private histogram in
-// shared memory (one copy per warp, against contention on the same bins),
-// reads its tile with 16-byte loads, and adds its partial sums to the
-// global 64-bit totals with one atomic per bin and per sum.
+// One pass over the data.  Each CTA keeps a private histogram in shared
+// memory (one copy per warp, against contention on the same bins), reads its
+// tile with 16-byte loads, forms the sums of products four bytes at a time
+// with the unsigned 4-way byte dot product (__dp4a), and adds its partial
+// sums to the global 64-bit totals with one atomic per bin and per sum.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,40 +37,69 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
 
   for (uint64_t base = (uint64_t)blockIdx.x * kTile; base < n; base += (uint64_t)gridDim.x * kTile) {
     const uint64_t end = base + kTile < n ? base + kTile : n;
-    // each thread takes 16 consecutive bytes at a time
-    for (uint64_t i = base + 16ull * threadIdx.x; i < end; i += 16ull * kThreads) {
-      uint8_t v[16 + LC_STATS_MAX_LAG];
-      const uint64_t cnt = end - i < 16 ? end - i : 16;
-      if (cnt == 16 && ((reinterpret_cast<uintptr_t>(data + i) & 15u) == 0)) {
-        const uint4 q = *reinterpret_cast<const uint4*>(data + i);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    // 32-bit partial sums per tile: a thread adds at most 16 groups of 16
+    // bytes per tile, so every partial stays below 256 * 255^2 < 2^32.
+    uint32_t t1 = 0, t2 = 0;
+    uint32_t tl[LC_STATS_MAX_LAG];
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
+    for (int k = 0; k < LC_STATS_MAX_LAG; k++) tl[k] = 0;
+    // each thread takes 16 consecutive bytes at a time, as 4 words, plus the
+    // next 8 bytes (2 words) for the lagged products; bytes at or past the
+    // end of the data read as 0 and add nothing
+    for (uint64_t i = base + 16ull * threadIdx.x; i < end; i += 16ull * kThreads) {
+      uint32_t w[6];
+      const uint64_t cnt = end - i < 16 ? end - i : 16;
+      const bool aligned = (reinterpret_cast<uintptr_t>(data + i) & 15u) == 0;
+      if (cnt == 16 && aligned) {
+        const uint4 q = *reinterpret_cast<const uint4*>(data + i);
+        w[0] = q.x;
+        w[1] = q.y;
+        w[2] = q.z;
+        w[3] = q.w;
       } else {
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = j < (int)cnt ? data[i + j] : 0;
-      }
-      // the bytes after this group, for the lagged products (may cross tiles)
+        for (int j = 0; j < 4; j++) {
+          uint32_t v = 0;
 #pragma unroll
-      for (int k = 0; k < LC_STATS_MAX_LAG; k++) {
-        const uint64_t p = i + 16 + k;
-        v[16 + k] = (k < (int)max_lag && p < n) ? data[p] : 0;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; j++) {
-        if (j < (int)cnt) {
-          const uint32_t x = v[j];
-          atomicAdd(&hist[warp][x], 1u);
-          s1 += x;
-          s2 += x * x;
-#pragma unroll
-          for (int k = 0; k < LC_STATS_MAX_LAG; k++) {
-            // x_{i+j} x_{i+j+k+1}; bytes past the end were read as 0
-            lag[k] += (k < (int)max_lag) ? (uint64_t)(x * (uint32_t)v[j + k + 1]) : 0ull;
-          }
+          for (int b = 0; b < 4; b++)
+            if (4 * j + b < (int)cnt) v |= (uint32_t)data[i + 4 * j + b] << (8 * b);
+          w[j] = v;
         }
       }
+      if (aligned && i + 24 <= n) {
+        const uint2 h = *reinterpret_cast<const uint2*>(data + i + 16);
+        w[4] = h.x;
+        w[5] = h.y;
+      } else {
+#pragma unroll
+        for (int j = 4; j < 6; j++) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int b = 0; b < 4; b++)
+            if (i + 4 * j + b < n) v |= (uint32_t)data[i + 4 * j + b] << (8 * b);
+          w[j] = v;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        t1 = __dp4a(w[j], 0x01010101u, t1);
+        t2 = __dp4a(w[j], w[j], t2);
+#pragma unroll
+        for (int k = 1; k <= LC_STATS_MAX_LAG; k++) {
+          // the word of bytes x_{4j+k} .. x_{4j+k+3}
+          const int wi = j + (k >> 2), sh = 8 * (k & 3);
+          const uint32_t sw = sh ? __funnelshift_r(w[wi], w[wi + 1], sh) : w[wi];
+          tl[k - 1] = __dp4a(w[j], sw, tl[k - 1]);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+          if (4 * j + b < (int)cnt) atomicAdd(&hist[warp][(w[j] >> (8 * b)) & 255u], 1u);
+      }
     }
+    s1 += t1;
+    s2 += t2;
+#pragma unroll
+    for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k];
   }
   __syncthreads();
   for (int b = threadIdx.x; b < 256; b += kThreads) {
