@@ -165,15 +165,19 @@ lc_status lc_run_batch(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* s
 lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count,
                             int32_t* status_host, lc_mode m, void* stream);
 
-/* Launch shape of the batched kernel: threads per CTA (32..1024, multiple of
+/* Launch shape of the batched kernel: threads per CTA (32..256, multiple of
  * 32), resident CTAs per SM for the persistent grid (0 = as many as fit),
- * and 1 to stage input through shared memory (0 = direct 16-byte loads).
- * The shape never changes results. */
+ * smem_staging (reserved, must be 0), and small_batch_rows: with the
+ * default constants, a batch of fewer parts than this runs the kernel
+ * variant that keeps all binary64 work on the FP64 pipe (lower latency
+ * while the GPU is far from full); larger batches run the variant that
+ * moves the multiplies to the integer pipes (higher throughput).  0 = auto
+ * (192 parts per SM).  The shape never changes results. */
 typedef struct {
   uint32_t threads_per_cta;
   uint32_t ctas_per_sm;
   uint32_t smem_staging;
-  uint32_t reserved;
+  uint32_t small_batch_rows;
 } lc_launch;
 
 lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out);

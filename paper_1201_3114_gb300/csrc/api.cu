@@ -71,13 +71,16 @@ struct lc_ctx {
   int slot = 0;
 
   cudaStream_t cap_stream = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t ev_node_a = nullptr, ev_node_b = nullptr;
-  bool graph_valid = false;
+  // one captured graph per kernel variant
+  struct GraphSlot {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_node_a = nullptr, ev_node_b = nullptr;
+    bool valid = false;
+    int grid = 0;
+  } graphs[kNumVariants];
 
   lc_launch launch{256, 0, 0, 0};
-  int grid = 0;
 
   std::unordered_map<std::string, HostKey> keys;
 
@@ -194,12 +197,18 @@ lc_status grow_device(T** ptr, size_t* cap, size_t need_elems, bool* changed) {
 }
 
 void release_graph(lc_ctx* ctx) {
-  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
-  if (ctx->graph) cudaGraphDestroy(ctx->graph);
-  ctx->exec = nullptr;
-  ctx->graph = nullptr;
-  ctx->ev_node_a = ctx->ev_node_b = nullptr;
-  ctx->graph_valid = false;
+  for (auto& g : ctx->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+    g.ev_node_a = g.ev_node_b = nullptr;
+    g.valid = false;
+  }
+}
+
+void invalidate_graphs(lc_ctx* ctx) {
+  for (auto& g : ctx->graphs) g.valid = false;
 }
 
 lc_status event_pair(lc_ctx* ctx, EventPair* ep) {
@@ -226,26 +235,32 @@ lc_status drain_timing(lc_ctx* ctx) {
   return LC_OK;
 }
 
-int resident_ctas(lc_ctx* ctx, int threads) {
+int resident_ctas(int variant, int threads) {
   int per_sm = 0;
-  const void* fn = batch_kernel_ptr(ctx->variant);
+  const void* fn = batch_kernel_ptr(variant);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads,
-                                                    batch_kernel_smem(ctx->variant)) != cudaSuccess ||
+                                                    batch_kernel_smem(variant)) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return per_sm;
 }
 
-// Graph: clear the counter and fail flags -> event A -> persistent cipher
-// kernel -> event B -> finalize.  Kernel arguments are fixed workspace
-// pointers; the per-batch sizes live in the uploaded header, so replays
-// need no re-capture until the workspace moves or the shape changes.
-lc_status build_graph(lc_ctx* ctx) {
-  release_graph(ctx);
+// Graph of variant v: clear the counter and fail flags -> event A ->
+// persistent cipher kernel -> event B -> finalize.  Kernel arguments are
+// fixed workspace pointers; the per-batch sizes live in the uploaded header,
+// so replays need no re-capture until the workspace moves or the shape
+// changes.
+lc_status build_graph(lc_ctx* ctx, int v) {
+  auto& G = ctx->graphs[v];
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (G.graph) cudaGraphDestroy(G.graph);
+  G.exec = nullptr;
+  G.graph = nullptr;
+  G.valid = false;
   const int threads = (int)ctx->launch.threads_per_cta;
-  int per_sm = resident_ctas(ctx, threads);
+  int per_sm = resident_ctas(v, threads);
   if (ctx->launch.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)ctx->launch.ctas_per_sm);
-  ctx->grid = ctx->sm_count * per_sm;
+  G.grid = ctx->sm_count * per_sm;
 
   EventPair ep;
   lc_status st = event_pair(ctx, &ep);
@@ -257,8 +272,7 @@ lc_status build_graph(lc_ctx* ctx) {
   cudaError_t e = cudaMemsetAsync(ctx->scratch_dev, 0, (4 + ctx->fail_cap) * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.a, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
-    e = launch_batch(ctx->variant, ctx->grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams,
-                     ctx->theta_dev, s);
+    e = launch_batch(v, G.grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams, ctx->theta_dev, s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.b, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
     e = launch_finalize(kFinalizeGrid, ctx->ws_dev, ctx->scratch_dev, ctx->params.block_len, s);
@@ -268,7 +282,7 @@ lc_status build_graph(lc_ctx* ctx) {
     if (g) cudaGraphDestroy(g);
     return cuda_fail(e != cudaSuccess ? e : e2);
   }
-  ctx->graph = g;
+  G.graph = g;
   size_t nn = 0;
   LC_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
@@ -279,13 +293,22 @@ lc_status build_graph(lc_ctx* ctx) {
     if (ty == cudaGraphNodeTypeEventRecord) {
       cudaEvent_t ev;
       LC_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
-      if (ev == ep.a) ctx->ev_node_a = nd;
-      if (ev == ep.b) ctx->ev_node_b = nd;
+      if (ev == ep.a) G.ev_node_a = nd;
+      if (ev == ep.b) G.ev_node_b = nd;
     }
   }
-  LC_CUDA(cudaGraphInstantiate(&ctx->exec, g, 0));
-  ctx->graph_valid = true;
+  LC_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
+  G.valid = true;
   return LC_OK;
+}
+
+// Kernel variant for a batch of nrows parts: v1 batches that cannot fill
+// the GPU run the latency variant.
+int batch_variant(const lc_ctx* ctx, size_t nrows) {
+  if (ctx->variant != kVariantV1) return ctx->variant;
+  const uint64_t thr = ctx->launch.small_batch_rows ? ctx->launch.small_batch_rows
+                                                    : (uint64_t)ctx->sm_count * kSmallBatchRowsPerSm;
+  return nrows < thr ? kVariantV1Latency : kVariantV1;
 }
 
 // Host validation of one request; LC_OK or the request's status code.
@@ -375,8 +398,9 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   const size_t bytes = sizeof(DevHeader) + count * sizeof(DevMsg) + nrows * sizeof(DevRow) +
                        count * sizeof(int32_t);
 
-  // Device workspace (graph is rebuilt whenever a buffer moves).
-  bool changed = !ctx->graph_valid;
+  // Device workspace (graphs are rebuilt whenever a buffer moves).
+  const int v = batch_variant(ctx, nrows);
+  bool changed = false;
   lc_status st = grow_device(&ctx->ws_dev, &ctx->ws_cap, bytes, &changed);
   if (st != LC_OK) return st;
   size_t fail_need = std::max<size_t>(count, 1024);
@@ -390,10 +414,12 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
     ctx->fail_cap = cap_words - 4;
     changed = true;
   }
-  if (changed) {
-    st = build_graph(ctx);
+  if (changed) invalidate_graphs(ctx);
+  if (!ctx->graphs[v].valid) {
+    st = build_graph(ctx, v);
     if (st != LC_OK) return st;
   }
+  auto& G = ctx->graphs[v];
 
   // Pinned staging, double-buffered: wait until the copy that last used
   // this slot has left it.
@@ -414,6 +440,7 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   hdr.nrows = (uint32_t)nrows;
   hdr.nmsgs = (uint32_t)count;
   hdr.status_out = status_dev;
+  hdr.rows_per_warp = rows_per_warp(nrows, (uint64_t)G.grid * (ctx->launch.threads_per_cta / 32));
   uint8_t* w = sg.host;
   memcpy(w, &hdr, sizeof hdr);
   w += sizeof hdr;
@@ -431,15 +458,15 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
     EventPair ep;
     st = event_pair(ctx, &ep);
     if (st != LC_OK) return st;
-    LC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ctx->exec, ctx->ev_node_a, ep.a));
-    LC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ctx->exec, ctx->ev_node_b, ep.b));
+    LC_CUDA(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_node_a, ep.a));
+    LC_CUDA(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_node_b, ep.b));
     ctx->ev_pending.push_back(ep);
     if (ctx->ev_pending.size() > 4096) {
       st = drain_timing(ctx);
       if (st != LC_OK) return st;
     }
   }
-  LC_CUDA(cudaGraphLaunch(ctx->exec, s));
+  LC_CUDA(cudaGraphLaunch(G.exec, s));
   ctx->launches += 2;  // cipher kernel + finalize kernel
   return LC_OK;
 }
@@ -520,7 +547,7 @@ lc_status lc_ctx_create(int device, lc_ctx** out) {
     e = cudaMemcpy(ctx->theta_dev, th.data(), kThetaEntries * sizeof(double), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) {
-    for (int v = kVariantGeneral; v <= kVariantV1; v++) {
+    for (int v = 0; v < kNumVariants; v++) {
       e = cudaFuncSetAttribute(batch_kernel_ptr(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)batch_kernel_smem(v));
       if (e != cudaSuccess) break;
@@ -568,7 +595,7 @@ lc_status lc_ctx_set_params(lc_ctx* ctx, const lc_params* p) {
   to_dev_params(*p, &ctx->dparams);
   ctx->variant = kernel_variant(ctx->dparams);
   ctx->keys.clear();
-  ctx->graph_valid = false;
+  invalidate_graphs(ctx);
   return LC_OK;
 }
 
@@ -725,10 +752,9 @@ lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out) {
 lc_status lc_ctx_set_launch(lc_ctx* ctx, const lc_launch* l) {
   if (!ctx || !l) return LC_ERR_ARG;
   if (l->threads_per_cta < 32 || l->threads_per_cta > 256 || l->threads_per_cta % 32) return LC_ERR_ARG;
-  if (l->ctas_per_sm > 64 || l->smem_staging > 1) return LC_ERR_ARG;
+  if (l->ctas_per_sm > 64 || l->smem_staging != 0) return LC_ERR_ARG;
   ctx->launch = *l;
-  ctx->launch.reserved = 0;
-  ctx->graph_valid = false;
+  invalidate_graphs(ctx);
   return LC_OK;
 }
 
@@ -755,13 +781,13 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e1));
   for (uint32_t tpc : tpcs) {
     if (st != LC_OK) break;
-    const int maxc = resident_ctas(ctx, (int)tpc);
+    const int maxc = resident_ctas(ctx->variant, (int)tpc);
     std::vector<uint32_t> cands = {0};
     for (uint32_t c = 1; c < (uint32_t)maxc; c *= 2) cands.push_back(c);
     for (uint32_t c : cands) {
-      lc_launch l{tpc, c, 0, 0};
+      lc_launch l{tpc, c, 0, saved.small_batch_rows};
       ctx->launch = l;
-      ctx->graph_valid = false;
+      invalidate_graphs(ctx);
       int32_t* stat = nullptr;
       st = ensure_status_tmp(ctx, 1);
       if (st != LC_OK) break;
@@ -785,7 +811,7 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   cudaStreamSynchronize(s);
   cudaFree(buf);
   ctx->launch = (st == LC_OK) ? bestl : saved;
-  ctx->graph_valid = false;
+  invalidate_graphs(ctx);
   if (best) *best = ctx->launch;
   return st;
 }

@@ -359,13 +359,31 @@ __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_
   uint32_t* counter = scratch;
   uint32_t* fail = scratch + 4;
 
+  // First pass: warp w of CTA c takes rows [(w * gridDim.x + c) * R, + R),
+  // interleaving CTAs (and hence SMs) first, so a batch with fewer rows than
+  // threads still spreads over the whole GPU.  Lanes >= R idle in this pass.
+  // Then rows are pulled dynamically, in warp-aggregated grabs, from R times
+  // the number of warps in the grid onwards.
+  const uint32_t R = H->rows_per_warp;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps_per_cta = blockDim.x >> 5;
+  const uint32_t static_rows = R * warps_per_cta * gridDim.x;
+  uint32_t r = lane < R ? ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * R + lane : 0xFFFFFFFFu;
+  bool first = true;
   while (true) {
-    cg::coalesced_group g = cg::coalesced_threads();
-    uint32_t base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(counter, g.size());
-    base = g.shfl(base, 0);
-    const uint32_t r = base + g.thread_rank();
-    if (r >= nrows) break;
+    if (!first) {
+      cg::coalesced_group g = cg::coalesced_threads();
+      uint32_t base = 0;
+      if (g.thread_rank() == 0) base = atomicAdd(counter, g.size());
+      base = g.shfl(base, 0);
+      r = static_rows + base + g.thread_rank();
+      if (r >= nrows) break;
+    }
+    first = false;
+    if (r >= nrows) {
+      if (lane >= R) break;  // idle lane of an under-filled batch
+      continue;              // static row past the end: go to the dynamic grab
+    }
     const DevRow row = rows[r];
     DevMsg M;
     load_msg(M, msgs + row.msg);
@@ -440,6 +458,7 @@ __global__ void synth_kernel(uint8_t* __restrict__ dst, uint64_t n, uint64_t see
 using KGeneral = GeneralPath<false>;
 using KGeneral4 = GeneralPath<true>;
 using KV1 = V1Path<LC_EMU_MASK>;
+using KV1Lat = V1Path<0u>;
 
 }  // namespace
 
@@ -461,6 +480,7 @@ const void* batch_kernel_ptr(int variant) {
   switch (variant) {
     case kVariantGeneral: return reinterpret_cast<const void*>(&batch_kernel<KGeneral>);
     case kVariantGeneral4: return reinterpret_cast<const void*>(&batch_kernel<KGeneral4>);
+    case kVariantV1Latency: return reinterpret_cast<const void*>(&batch_kernel<KV1Lat>);
     default: return reinterpret_cast<const void*>(&batch_kernel<KV1>);
   }
 }
@@ -471,6 +491,7 @@ cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, ui
   switch (variant) {
     case kVariantGeneral: batch_kernel<KGeneral><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
     case kVariantGeneral4: batch_kernel<KGeneral4><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
+    case kVariantV1Latency: batch_kernel<KV1Lat><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
     default: batch_kernel<KV1><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
   }
   return cudaGetLastError();

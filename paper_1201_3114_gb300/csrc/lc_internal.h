@@ -21,6 +21,14 @@ constexpr int kThetaEntries = kMaxK * 256;
 constexpr int kVariantGeneral = 0;
 constexpr int kVariantGeneral4 = 1;
 constexpr int kVariantV1 = 2;
+// The v1 constants with every binary64 operation on the FP64 pipe: shorter
+// dependency chains, hence lower latency while the GPU is far from full.
+constexpr int kVariantV1Latency = 3;
+constexpr int kNumVariants = 4;
+
+// Below this many parts per SM (1.5 warps per SM sub-partition) a v1 batch
+// runs the latency variant (measured crossover on GB300).
+constexpr uint32_t kSmallBatchRowsPerSm = 4 * 32 * 3 / 2;
 
 // Constants of the method as the kernels read them.
 struct DevParams {
@@ -58,10 +66,18 @@ struct DevRow {
 struct alignas(16) DevHeader {
   uint32_t nrows;
   uint32_t nmsgs;
-  int32_t* status_out;  // caller's status array (device)
-  uint64_t reserved[2];
+  int32_t* status_out;     // caller's status array (device)
+  uint32_t rows_per_warp;  // R: rows a warp takes per grab (1..32, see kernel)
+  uint32_t reserved0;
+  uint64_t reserved1;
 };
 static_assert(sizeof(DevHeader) == 32, "DevHeader layout");
+
+// R: rows a warp takes per grab.  A warp instruction costs the FP64 pipe
+// and the issue slot as much with one active lane as with 32 (measured), so
+// rows are packed into full warps (R = 32) and it is the warps that are
+// spread over the SMs (see the kernel's first pass).
+inline uint32_t rows_per_warp(uint64_t /*nrows*/, uint64_t /*grid_warps*/) { return 32u; }
 
 // Persistent-kernel scratch that lives across launches: the row counter and
 // the per-message fail flags.  The finalize kernel clears both after use.

@@ -180,6 +180,15 @@ extern "C" lc_status lc_run_batch_noalloc(const lc_req* reqs, size_t count, int3
   const size_t bytes = sizeof(DevHeader) + count * sizeof(DevMsg) + w * sizeof(DevRow) +
                        count * sizeof(int32_t);
 
+  int sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LC_ERR_CUDA;
+  const int variant = w < (size_t)sms * kSmallBatchRowsPerSm ? kVariantV1Latency : kVariantV1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_ptr(variant), 256,
+                                                    batch_kernel_smem(variant)) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  hdr.rows_per_warp = rows_per_warp(w, (uint64_t)sms * per_sm * 8);
+  memcpy(g_host_ws, &hdr, sizeof hdr);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint8_t* ws = base + kWsOff;
   uint32_t* flags = reinterpret_cast<uint32_t*>(base);
@@ -188,13 +197,7 @@ extern "C" lc_status lc_run_batch_noalloc(const lc_req* reqs, size_t count, int3
   // so the host image may be rebuilt by the next call.
   if (cudaMemcpyAsync(ws, g_host_ws, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return LC_ERR_CUDA;
   if (cudaMemsetAsync(flags, 0, (4 + count) * sizeof(uint32_t), s) != cudaSuccess) return LC_ERR_CUDA;
-  int sms = 0, per_sm = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LC_ERR_CUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_ptr(kVariantV1), 256,
-                                                    batch_kernel_smem(kVariantV1)) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  if (launch_batch(kVariantV1, sms * per_sm, 256, ws, flags, dp, theta, s) != cudaSuccess) return LC_ERR_CUDA;
+  if (launch_batch(variant, sms * per_sm, 256, ws, flags, dp, theta, s) != cudaSuccess) return LC_ERR_CUDA;
   if (launch_finalize(256, ws, flags, p.block_len, s) != cudaSuccess) return LC_ERR_CUDA;
   return LC_OK;
 }

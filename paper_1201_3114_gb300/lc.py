@@ -55,7 +55,7 @@ class lc_launch(C.Structure):
         ("threads_per_cta", C.c_uint32),
         ("ctas_per_sm", C.c_uint32),
         ("smem_staging", C.c_uint32),
-        ("reserved", C.c_uint32),
+        ("small_batch_rows", C.c_uint32),
     ]
 
 
@@ -347,8 +347,9 @@ def lc_ctx_get_launch(ctx) -> lc_launch:
     return l
 
 
-def lc_ctx_set_launch(ctx, threads_per_cta=256, ctas_per_sm=0, smem_staging=0) -> int:
-    l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, 0)
+def lc_ctx_set_launch(ctx, threads_per_cta=256, ctas_per_sm=0, smem_staging=0,
+                      small_batch_rows=0) -> int:
+    l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, small_batch_rows)
     return load().lc_ctx_set_launch(ctx, C.byref(l))
 
 

@@ -327,11 +327,46 @@ def test_launch_shapes_do_not_change_results(ctx):
     want = O.encrypt(pw, P)
     try:
         for tpc, cps in ((32, 1), (64, 0), (128, 2), (256, 0)):
-            assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps) == lc.LC_OK
-            assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps)
+            for small in (1, 0xFFFFFFFF):  # integer-split variant, FP64-only variant
+                assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small) == lc.LC_OK
+                assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small)
+        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 1, 0) == lc.LC_ERR_ARG
         best = lc.lc_tune(ctx.handle, 8 << 20)
         assert best.threads_per_cta in (64, 128, 256)
         assert np.array_equal(gpu_encrypt(ctx, pw, P), want)
+    finally:
+        lc.lc_ctx_set_launch(ctx.handle, 256, 0)
+
+
+@pytest.mark.parametrize("small", [1, 0xFFFFFFFF], ids=["int-split", "fp64-only"])
+def test_both_v1_kernel_variants(ctx, small):
+    # The batched kernel has two v1 variants (binary64 multiplies on the
+    # integer pipes, or everything on the FP64 pipe); force each one.
+    try:
+        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, small) == lc.LC_OK
+        for i, n in enumerate([0, 1, 17, B - 1, B + 1, 5 * B + 3]):
+            for mode in (lc.LC_PARALLEL, lc.LC_SEQUENTIAL):
+                pw = synth.password(synth.subseed(60, i), 2 + 5 * i)
+                P = synth.uniform_bytes(synth.subseed(61, i), n)
+                want = O.encrypt(pw, P, mode)
+                got = gpu_encrypt(ctx, pw, P, mode)
+                assert np.array_equal(got, want), (small, n, mode)
+                st, back = gpu_decrypt(ctx, pw, got, mode)
+                assert st == lc.LC_OK and np.array_equal(back, P)
+        msgs = _mixed_batch(64, 62)
+        items, expect = [], []
+        for pw, d, P in msgs:
+            ct = O.encrypt(pw, P)
+            src = dev(P if d == 0 else ct)
+            want = ct if d == 0 else P
+            out = torch.zeros(max(1, want.size), dtype=torch.uint8, device="cuda")
+            items.append((pw, d, src, src.numel(), out, want.size))
+            expect.append(want)
+        status = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+        lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(items), status))
+        assert (host(status) == 0).all()
+        for k, want in enumerate(expect):
+            assert np.array_equal(host(items[k][4])[:want.size], want), k
     finally:
         lc.lc_ctx_set_launch(ctx.handle, 256, 0)
 
