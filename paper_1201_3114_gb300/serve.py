@@ -115,13 +115,17 @@ class Server:
     """Continuous-batching request loop over ``streams`` CUDA streams."""
 
     def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
-                 max_batch_bytes=1 << 30, max_batch_requests=8192, replay_cap_bytes=None,
+                 max_batch_bytes=256 << 20, max_batch_requests=8192, replay_cap_bytes=None,
                  seed=0x5E4E):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
         self.ctxs = [lc.Context(device) for _ in range(streams)]
+        # Batches on different streams share the GPU, so even a small batch
+        # runs the throughput (integer-split) kernel variant.
+        for c in self.ctxs:
+            lc.check(lc.lc_ctx_set_launch(c.handle, 256, 0, 0, 1), "lc_ctx_set_launch")
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.arena = Arena(budget_bytes, self.device)
         self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
@@ -135,6 +139,23 @@ class Server:
                             for _ in range(streams)]
         self.reqs = [np.zeros(max_batch_requests, dtype=REQ_DTYPE) for _ in range(streams)]
         torch.cuda.synchronize()
+        self.warmup()
+
+    def warmup(self, nbytes=32 << 20):
+        """Run one batch per stream before serving, so that graph capture and
+        workspace growth do not land on the first requests."""
+        torch = self.torch
+        n = min(nbytes, self.pool.numel())
+        out = self.arena.alloc(ct_len(n))
+        try:
+            for s, c in enumerate(self.ctxs):
+                with torch.cuda.stream(self.streams[s]):
+                    lc.check(lc.lc_encrypt(c.handle, b"warm-up-password", self.pool.data_ptr(), n,
+                                           self.arena.base + out[0], ct_len(n), lc.LC_PARALLEL,
+                                           self.streams[s]), "warm-up")
+                torch.cuda.synchronize()
+        finally:
+            self.arena.release(out)
 
     def close(self):
         for c in self.ctxs:
