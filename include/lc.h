@@ -158,8 +158,9 @@ lc_status lc_run_batch(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* s
 
 /* lc_run_batch with HOST buffers: `in` / `out` are host pointers (pinned
  * memory gives the best copy rate) and status_host is host memory.  The
- * library copies the inputs to its own device staging area, runs the batch
- * and copies the outputs and statuses back; returns after the stream has
+ * library copies the inputs to its own device staging area (one copy per
+ * run of requests whose host buffers are contiguous), runs the batch and
+ * copies the outputs and statuses back; returns after the stream has
  * synchronised.  The call's return value is LC_OK unless the call itself
  * failed; per-request results are in status_host. */
 lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count,

@@ -472,3 +472,34 @@ def test_n_it_steps_per_byte_profile():
             assert np.array_equal(got, want), n
             st, back = gpu_decrypt(c, pw, got)
             assert st == lc.LC_OK and np.array_equal(back, P)
+
+
+def test_host_buffer_batch_pageable_and_scattered(ctx):
+    # Pageable numpy buffers (one per request, not contiguous) take the
+    # staging path; page-locked ones the zero-copy path.  Both equal the oracle.
+    msgs = _mixed_batch(24, 63, max_size=20000)
+    ins, outs, want = [], [], []
+    for pw, d, P in msgs:
+        ct = O.encrypt(pw, P)
+        ins.append(np.ascontiguousarray(P if d == 0 else ct))
+        want.append(ct if d == 0 else P)
+        outs.append(np.zeros(max(1, want[-1].size), dtype=np.uint8))
+    items = [(pw, d, x, x.size, y, w.size) for (pw, d, _), x, y, w in zip(msgs, ins, outs, want)]
+    st = np.full(len(items), -1, dtype=np.int32)
+    lc.check(lc.lc_run_batch_host(ctx.handle, lc.Batch(items), st))
+    assert (st == 0).all()
+    for y, w in zip(outs, want):
+        assert np.array_equal(y[:w.size], w)
+    # the same requests from page-locked buffers, a tampered one among them
+    pins = [torch.from_numpy(x.copy()).pin_memory() for x in ins]
+    pouts = [torch.zeros(max(1, w.size), dtype=torch.uint8).pin_memory() for w in want]
+    k = next(i for i, (_, d, P) in enumerate(msgs) if d == 1 and P.size > 0)
+    pins[k][0] ^= 1
+    items = [(pw, d, x, x.numel(), y, w.size) for (pw, d, _), x, y, w in zip(msgs, pins, pouts, want)]
+    st = np.full(len(items), -1, dtype=np.int32)
+    lc.check(lc.lc_run_batch_host(ctx.handle, lc.Batch(items), st))
+    for i, (y, w) in enumerate(zip(pouts, want)):
+        if i == k:
+            assert st[i] == lc.LC_ERR_INTEGRITY and not y.numpy().any()
+        else:
+            assert st[i] == 0 and np.array_equal(y.numpy()[:w.size], w), i
