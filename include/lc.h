@@ -82,6 +82,11 @@ uint32_t lc_version(void);
 /* Static English text for a status code (never NULL). */
 const char* lc_status_string(lc_status s);
 
+/* Text of the last CUDA failure a call of this thread turned into
+ * LC_ERR_CUDA / LC_ERR_NOMEM: the CUDA error, the failing call and its
+ * place ("" if none).  Valid until the thread's next failing call. */
+const char* lc_last_cuda_error(void);
+
 /* The default ("v1") constants described above. */
 lc_status lc_params_default(lc_params* out);
 

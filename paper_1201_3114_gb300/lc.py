@@ -102,7 +102,10 @@ class lc_byte_stats_t(C.Structure):
 class LcError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
-        super().__init__("%s: %s (status %d)" % (what, status_string(status), status))
+        detail = ""
+        if status in (LC_ERR_CUDA, LC_ERR_NOMEM):
+            detail = " [%s]" % load().lc_last_cuda_error().decode()
+        super().__init__("%s: %s (status %d)%s" % (what, status_string(status), status, detail))
 
 
 _lib = None
@@ -111,6 +114,7 @@ _lock = threading.Lock()
 _SIGNATURES = {
     "lc_version": (C.c_uint32, []),
     "lc_status_string": (C.c_char_p, [C.c_int]),
+    "lc_last_cuda_error": (C.c_char_p, []),
     "lc_params_default": (C.c_int, [C.POINTER(lc_params)]),
     "lc_ctx_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
     "lc_ctx_destroy": (None, [C.c_void_p]),
@@ -244,6 +248,10 @@ def lc_version() -> int:
 
 def lc_status_string(status: int) -> str:
     return status_string(status)
+
+
+def lc_last_cuda_error() -> str:
+    return load().lc_last_cuda_error().decode()
 
 
 def lc_params_default() -> lc_params:
