@@ -64,7 +64,8 @@ typedef enum { LC_ENCRYPT = 0, LC_DECRYPT = 1 } lc_dir;
  * n_it read as the warm-up length).  Layout mirrors the oracle's. */
 typedef struct {
   double sigma, rho, beta; /* Lorenz parameters, Sec. 3.1 */
-  double dt;               /* Euler step, Sec. 3.1 (0 < dt <= 0.027) */
+  double dt;               /* Euler step; Sec. 3.1 bounds it by 0 < dt <= 0.027, the
+                              library takes any non-NaN value (0 freezes r) */
   uint32_t n_warm;         /* Euler steps before the first byte */
   uint32_t steps_per_byte; /* applications of F per byte (1..4096) */
   double lambda[3];        /* offset of r_0, Eq. 5 */
