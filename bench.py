@@ -178,13 +178,17 @@ def fp64_pipe_ops_per_launch(sizes, mask, n_warm=3000, steps=1, B=4096, T=8):
     return int(parts.sum()) * per_part + int(traj_bytes.sum()) * per_byte
 
 
+# the translation unit of the cipher kernel: the sources its code comes from
+KERNEL_SOURCES = ("paper_1201_3114_gb300/csrc/cipher.cu", "paper_1201_3114_gb300/csrc/softfp64.cuh",
+                  "paper_1201_3114_gb300/csrc/lc_internal.h", "include/lc.h")
+
+
 def source_hash():
+    """Hash of the cipher kernel's sources (keys the committed ncu traffic)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1201_3114_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".h", ".cpp")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()[:16]
 
 
