@@ -8,8 +8,10 @@ schedules (cached), the flattened part table, the persistent cipher kernel
 and the verdict/finalize kernel, replayed from a CUDA graph.
 
   value   message bytes / second over K timed steps, inputs resident in HBM
-  e2e     the same through lc_run_batch_host: pinned host buffers in and out,
-          host<->device copies inside the timed region
+  e2e     the same from pinned host buffers, host<->device copies inside the
+          timed region: lc_submit_batch_host / lc_wait_batch_host with step k+1
+          submitted before step k's results are read (sync_value: one
+          synchronous lc_run_batch_host per step)
   roofline  the cipher kernel's FP64 operation rate against the FP64 issue
           peak (the kernel is bound by binary64 arithmetic, not HBM)
   per_message_launch  a sample of the same messages launched one per call
@@ -378,7 +380,7 @@ def profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--messages", type=int, default=4096)
@@ -554,29 +556,58 @@ def main():
         hin_tot = sum(it[3] for it in items)
         hout_tot = sum(it[5] for it in items)
         hin = torch.empty(hin_tot, dtype=torch.uint8).pin_memory()
-        hout = torch.empty(hout_tot, dtype=torch.uint8).pin_memory()
-        hitems, a, b_ = [], 0, 0
+        # two sets of outputs and statuses: a step's results stay intact while
+        # the next step's copies run
+        houts = [torch.empty(hout_tot, dtype=torch.uint8).pin_memory() for _ in range(2)]
+        hitems = [[], []]
+        a, b_ = 0, 0
         for m, it in enumerate(items):
             src = Parena if it[1] == 0 else Carena
             off = (p_off[m] if it[1] == 0 else c_off[m])
             hin[a:a + it[3]].copy_(src[off:off + it[3]])
-            hitems.append((it[0], it[1], hin.data_ptr() + a, it[3], hout.data_ptr() + b_, it[5]))
+            for j in range(2):
+                hitems[j].append((it[0], it[1], hin.data_ptr() + a, it[3], houts[j].data_ptr() + b_, it[5]))
             a += it[3]
             b_ += it[5]
-        hbatch = lc.Batch(hitems)
-        hstat = np.zeros(count, dtype=np.int32)
-        for _ in range(2):
-            lc.check(lc.lc_run_batch_host(ctx.handle, hbatch, hstat, lc.LC_PARALLEL, stream))
-        assert (hstat == 0).all()
+        hbatches = [lc.Batch(hitems[j]) for j in range(2)]
+        hstats = [np.zeros(count, dtype=np.int32) for _ in range(2)]
+        for j in range(2):
+            lc.check(lc.lc_run_batch_host(ctx.handle, hbatches[j], hstats[j], lc.LC_PARALLEL, stream))
+            assert (hstats[j] == 0).all()
+        # one synchronous call per step
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            lc.check(lc.lc_run_batch_host(ctx.handle, hbatch, hstat, lc.LC_PARALLEL, stream))
+        for k in range(args.steps):
+            lc.check(lc.lc_run_batch_host(ctx.handle, hbatches[k % 2], hstats[k % 2], lc.LC_PARALLEL,
+                                          stream))
+            if not (hstats[k % 2] == 0).all():
+                raise RuntimeError("host-buffer batch failed")
+        t_sync = max_over_ranks(time.perf_counter() - t0, dev if ws > 1 else None)
+        # pipelined: step k+1 is submitted before step k's results are read,
+        # so its input copies overlap step k's kernel
+        barrier()
+        t0 = time.perf_counter()
+        prev = None
+        for k in range(args.steps):
+            rc, t = lc.lc_submit_batch_host(ctx.handle, hbatches[k % 2], hstats[k % 2], lc.LC_PARALLEL,
+                                            stream)
+            lc.check(rc, "lc_submit_batch_host")
+            if prev is not None:
+                lc.check(lc.lc_wait_batch_host(ctx.handle, prev[0]), "lc_wait_batch_host")
+                if not (hstats[prev[1]] == 0).all():
+                    raise RuntimeError("host-buffer batch failed")
+            prev = (t, k % 2)
+        lc.check(lc.lc_wait_batch_host(ctx.handle, prev[0]), "lc_wait_batch_host")
+        if not (hstats[prev[1]] == 0).all():
+            raise RuntimeError("host-buffer batch failed")
         t_e2e = max_over_ranks(time.perf_counter() - t0, dev if ws > 1 else None)
         e2e = {"value": ws * msg_bytes * args.steps / t_e2e / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": hin_tot, "d2h_bytes_per_step": hout_tot + 4 * count,
-               "call": "lc_run_batch_host"}
-        del hin, hout
+               "call": "lc_submit_batch_host + lc_wait_batch_host (step k+1 submitted before "
+                       "step k's results are read)",
+               "sync_value": ws * msg_bytes * args.steps / t_sync / 1e9,
+               "sync_call": "lc_run_batch_host (one synchronous call per step)"}
+        del hin, houts, hbatches
 
     # ---- served workload (continuous batching), rank 0
     served = None

@@ -172,6 +172,41 @@ lc_status lc_run_batch(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* s
 lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count,
                             int32_t* status_host, lc_mode m, void* stream);
 
+/* Host-buffer batches a context can hold in flight (one device staging area
+ * each). */
+#define LC_HOST_INFLIGHT 2u
+
+/* lc_run_batch_host without the wait, so that consecutive batches overlap:
+ * batch k+1's input copies run while batch k computes, and batch k's output
+ * copies while batch k+1 computes.  The paper has no counterpart; this is a
+ * pipelining aid of the library.
+ *
+ * The call validates and plans the batch, enqueues the input copies (on a
+ * copy stream of the context), the batch (on `stream`) and the output and
+ * status copies (on a second copy stream of the context), and returns with
+ * *ticket set to a number > 0 that increases per context.  Buffers: the
+ * request array and the passwords may be reused when the call returns; the
+ * host inputs must stay unchanged, and the host outputs and status_host
+ * hold undefined bytes, until lc_wait_batch_host returns for this ticket or
+ * a later one.  The inputs are read after the call returns, with no
+ * ordering against earlier work on `stream`: host buffers filled by
+ * asynchronous copies must be complete before the call.  Pinned host
+ * buffers keep every copy asynchronous; with pageable output buffers the
+ * call waits for the batch.  With LC_HOST_INFLIGHT batches already in
+ * flight, the call first waits for the oldest (which completes its ticket).
+ * count == 0 gives a ticket that is already complete.  Errors: LC_ERR_ARG
+ * (NULL ctx or ticket, NULL reqs or status_host with count > 0, a bad
+ * mode), otherwise as lc_run_batch_host; after an error nothing of this
+ * batch is in flight and *ticket must not be waited for. */
+lc_status lc_submit_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count,
+                               int32_t* status_host, lc_mode m, void* stream, uint64_t* ticket);
+
+/* Wait until the batch of `ticket`, and every batch submitted before it, has
+ * finished and its outputs and statuses are in host memory.  LC_OK if they
+ * already were; LC_ERR_ARG for ticket 0 or a ticket not yet issued;
+ * LC_ERR_CUDA if a copy or kernel of those batches failed. */
+lc_status lc_wait_batch_host(lc_ctx* ctx, uint64_t ticket);
+
 /* Launch shape of the batched kernel: threads per CTA (32..256, multiple of
  * 32), resident CTAs per SM for the persistent grid (0 = as many as fit),
  * smem_staging (reserved, must be 0), and small_batch_rows: with the

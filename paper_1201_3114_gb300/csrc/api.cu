@@ -49,6 +49,24 @@ struct Staging {
   bool used = false;
 };
 
+// Device staging of one host-buffer batch in flight.
+struct HostSlot {
+  uint8_t* io_dev = nullptr;  // the batch's inputs and outputs
+  size_t io_cap = 0;
+  int32_t* status_dev = nullptr;
+  size_t status_cap = 0;
+  // Statuses land in pinned memory first (a copy into pageable memory would
+  // make the enqueueing call wait for the batch) and reach the caller's
+  // array when the batch is retired.
+  int32_t* status_pinned = nullptr;
+  size_t status_pinned_cap = 0;
+  int32_t* status_user = nullptr;
+  size_t status_count = 0;
+  std::vector<cudaEvent_t> events;  // per chunk: inputs uploaded, chunk computed; + 1
+  cudaEvent_t done = nullptr;       // outputs and statuses are in host memory
+  uint64_t ticket = 0;              // the batch staged here, 0 if none
+};
+
 }  // namespace
 
 struct lc_ctx {
@@ -65,11 +83,10 @@ struct lc_ctx {
   size_t fail_cap = 0;              // messages covered by the fail flags
   int32_t* status_tmp_dev = nullptr;
   size_t status_tmp_cap = 0;
-  uint8_t* io_dev = nullptr;  // staging for lc_run_batch_host
-  size_t io_cap = 0;
   unsigned long long* stats_dev = nullptr;  // lc_byte_stats accumulators
-  cudaStream_t copy_in = nullptr, copy_out = nullptr;  // lc_run_batch_host pipeline
-  std::vector<cudaEvent_t> pipe_events;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;  // host-buffer batch copies
+  HostSlot hslots[LC_HOST_INFLIGHT];
+  uint64_t next_ticket = 1;
 
   Staging staging[2];
   int slot = 0;
@@ -593,12 +610,17 @@ void lc_ctx_destroy(lc_ctx* ctx) {
   if (ctx->ws_dev) cudaFree(ctx->ws_dev);
   if (ctx->scratch_dev) cudaFree(ctx->scratch_dev);
   if (ctx->status_tmp_dev) cudaFree(ctx->status_tmp_dev);
-  if (ctx->io_dev) cudaFree(ctx->io_dev);
+  for (auto& h : ctx->hslots) {
+    if (h.io_dev) cudaFree(h.io_dev);
+    if (h.status_dev) cudaFree(h.status_dev);
+    if (h.status_pinned) cudaFreeHost(h.status_pinned);
+    for (auto ev : h.events) cudaEventDestroy(ev);
+    if (h.done) cudaEventDestroy(h.done);
+  }
   if (ctx->stats_dev) cudaFree(ctx->stats_dev);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
   if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
-  for (auto ev : ctx->pipe_events) cudaEventDestroy(ev);
   delete ctx;
 }
 
@@ -677,13 +699,28 @@ lc_status lc_decrypt(lc_ctx* ctx, const uint8_t* pw, size_t pw_len, const uint8_
   return (lc_status)verdict;
 }
 
-lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_host,
-                            lc_mode m, void* stream) {
-  if (!ctx || (!reqs && count) || (!status_host && count)) return LC_ERR_ARG;
-  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
-  if (count == 0) return LC_OK;
-  DeviceGuard g(ctx->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// ---------------------------------------------------------------------------
+// Host-buffer batches: inputs are copied into a staging slot on the device,
+// the batch runs there, and outputs and statuses are copied back.  Each
+// batch in flight owns one of LC_HOST_INFLIGHT slots, so the copies of one
+// batch overlap the kernel of another.
+// ---------------------------------------------------------------------------
+
+// Wait for the batch staged in h, if any, hand its statuses over and free
+// the slot.
+static lc_status retire_slot(HostSlot& h) {
+  if (!h.ticket) return LC_OK;
+  h.ticket = 0;
+  LC_CUDA(cudaEventSynchronize(h.done));
+  memcpy(h.status_user, h.status_pinned, h.status_count * sizeof(int32_t));
+  return LC_OK;
+}
+
+// Enqueue one host-buffer batch into slot h.  after_stream: the input copies
+// also wait for the work already on s (the synchronous entry point's stream
+// semantics).
+static lc_status enqueue_host(lc_ctx* ctx, HostSlot& h, const lc_req* reqs, size_t count,
+                              int32_t* status_host, lc_mode m, cudaStream_t s, bool after_stream) {
   const lc_params& p = ctx->params;
 
   // Bytes each request will write: its full result, clipped to out_cap.
@@ -708,18 +745,18 @@ lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32
   size_t cursor = 0;
   auto plan = [&](bool input, std::vector<Run>& runs) {
     for (size_t i = 0; i < count;) {
-      const uint8_t* h = input ? reqs[i].in : reqs[i].out;
+      const uint8_t* hp = input ? reqs[i].in : reqs[i].out;
       size_t span = input ? reqs[i].in_len : out_len[i];
       size_t j = i + 1;
-      while (h && j < count) {
+      while (hp && j < count) {
         const uint8_t* hj = input ? reqs[j].in : reqs[j].out;
-        if (hj != h + span) break;
+        if (hj != hp + span) break;
         span += input ? reqs[j].in_len : out_len[j];
         j++;
       }
       cursor = (cursor + 255) & ~(size_t)255;
-      const size_t off = cursor + (reinterpret_cast<uintptr_t>(h) & 255u);
-      runs.push_back(Run{i, j, h, span, off});
+      const size_t off = cursor + (reinterpret_cast<uintptr_t>(hp) & 255u);
+      runs.push_back(Run{i, j, hp, span, off});
       cursor = off + span;
       i = j;
     }
@@ -727,18 +764,29 @@ lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32
   std::vector<Run> in_runs, out_runs;
   plan(true, in_runs);
   plan(false, out_runs);
-  lc_status st = grow_device(&ctx->io_dev, &ctx->io_cap, std::max<size_t>(cursor, 256), nullptr);
+  lc_status st = grow_device(&h.io_dev, &h.io_cap, std::max<size_t>(cursor, 256), nullptr);
   if (st != LC_OK) return st;
-  st = ensure_status_tmp(ctx, count);
+  st = grow_device(&h.status_dev, &h.status_cap, count, nullptr);
   if (st != LC_OK) return st;
+  if (h.status_pinned_cap < count) {
+    if (h.status_pinned) cudaFreeHost(h.status_pinned);
+    h.status_pinned = nullptr;
+    h.status_pinned_cap = 0;
+    const size_t cap = std::max<size_t>(count, 4096);
+    LC_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&h.status_pinned), cap * sizeof(int32_t),
+                          cudaHostAllocDefault));
+    h.status_pinned_cap = cap;
+  }
+  h.status_user = status_host;
+  h.status_count = count;
 
   std::vector<lc_req> dreq(reqs, reqs + count);
   for (const Run& r : in_runs)
     for (size_t k = r.first; k < r.last; k++)
-      dreq[k].in = r.h ? ctx->io_dev + r.dev_off + (reqs[k].in - r.h) : nullptr;
+      dreq[k].in = r.h ? h.io_dev + r.dev_off + (reqs[k].in - r.h) : nullptr;
   for (const Run& r : out_runs)
     for (size_t k = r.first; k < r.last; k++) {
-      dreq[k].out = r.h ? ctx->io_dev + r.dev_off + (reqs[k].out - r.h) : nullptr;
+      dreq[k].out = r.h ? h.io_dev + r.dev_off + (reqs[k].out - r.h) : nullptr;
       dreq[k].out_cap = out_len[k] < reqs[k].out_cap ? out_len[k] : reqs[k].out_cap;
     }
 
@@ -749,7 +797,7 @@ lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32
   // the resident grid runs a nearly empty second wave as long as a full
   // one, so chunks are only cut for batches of several grid waves (>= 4 GiB
   // per chunk); a 2 GB batch split in four ran 17.6 GB/s end to end against
-  // 22 GB/s as one launch.
+  // 22 GB/s as one launch.  Overlap between batches comes from the slots.
   size_t total_in = 0;
   for (size_t i = 0; i < count; i++) total_in += reqs[i].in_len;
   const size_t K = std::max<size_t>(1, std::min<size_t>(4, total_in / ((size_t)4 << 30)));
@@ -775,7 +823,7 @@ lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32
       const uint8_t* h1 = input ? reqs[hi - 1].in + reqs[hi - 1].in_len : reqs[hi - 1].out + out_len[hi - 1];
       const size_t len = (size_t)(h1 - h0);
       if (!len) continue;
-      uint8_t* d = ctx->io_dev + r.dev_off + (h0 - r.h);
+      uint8_t* d = h.io_dev + r.dev_off + (h0 - r.h);
       cudaError_t e = input ? cudaMemcpyAsync(d, h0, len, cudaMemcpyHostToDevice, cs)
                             : cudaMemcpyAsync(const_cast<uint8_t*>(h0), d, len, cudaMemcpyDeviceToHost, cs);
       if (e == cudaErrorInvalidValue) {
@@ -788,7 +836,7 @@ lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32
           const uint8_t* hk = input ? reqs[k].in : reqs[k].out;
           const size_t lk = input ? reqs[k].in_len : out_len[k];
           if (!lk) continue;
-          uint8_t* dk = ctx->io_dev + r.dev_off + (hk - r.h);
+          uint8_t* dk = h.io_dev + r.dev_off + (hk - r.h);
           e = input ? cudaMemcpyAsync(dk, hk, lk, cudaMemcpyHostToDevice, cs)
                     : cudaMemcpyAsync(const_cast<uint8_t*>(hk), dk, lk, cudaMemcpyDeviceToHost, cs);
         }
@@ -799,31 +847,96 @@ lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32
   };
   if (!ctx->copy_in) LC_CUDA(cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
   if (!ctx->copy_out) LC_CUDA(cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
-  while (ctx->pipe_events.size() < 2 * K + 1) {
+  while (h.events.size() < 2 * K + 1) {
     cudaEvent_t ev;
     LC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    ctx->pipe_events.push_back(ev);
+    h.events.push_back(ev);
   }
-  cudaEvent_t* evs = ctx->pipe_events.data();
-  // copies must not start before earlier work on `s` that may touch the arena
-  LC_CUDA(cudaEventRecord(evs[2 * K], s));
-  LC_CUDA(cudaStreamWaitEvent(ctx->copy_in, evs[2 * K], 0));
+  if (!h.done) LC_CUDA(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
+  cudaEvent_t* evs = h.events.data();
+  if (after_stream) {
+    LC_CUDA(cudaEventRecord(evs[2 * K], s));
+    LC_CUDA(cudaStreamWaitEvent(ctx->copy_in, evs[2 * K], 0));
+  }
   for (size_t c = 0; c + 1 < bound.size(); c++) {
     const size_t a = bound[c], b = bound[c + 1];
     LC_CUDA(copy_span(in_runs, true, a, b, ctx->copy_in));
     LC_CUDA(cudaEventRecord(evs[2 * c], ctx->copy_in));
     LC_CUDA(cudaStreamWaitEvent(s, evs[2 * c], 0));
-    st = run_batch_impl(ctx, dreq.data() + a, b - a, ctx->status_tmp_dev + a, m, s);
+    st = run_batch_impl(ctx, dreq.data() + a, b - a, h.status_dev + a, m, s);
     if (st != LC_OK) return st;
     LC_CUDA(cudaEventRecord(evs[2 * c + 1], s));
     LC_CUDA(cudaStreamWaitEvent(ctx->copy_out, evs[2 * c + 1], 0));
     LC_CUDA(copy_span(out_runs, false, a, b, ctx->copy_out));
   }
-  LC_CUDA(cudaMemcpyAsync(status_host, ctx->status_tmp_dev, count * sizeof(int32_t),
-                          cudaMemcpyDeviceToHost, s));
-  LC_CUDA(cudaStreamSynchronize(ctx->copy_out));
+  LC_CUDA(cudaMemcpyAsync(h.status_pinned, h.status_dev, count * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          ctx->copy_out));
+  LC_CUDA(cudaEventRecord(h.done, ctx->copy_out));
+  return LC_OK;
+}
+
+// Take a slot (waiting for the oldest batch if all are in use), enqueue the
+// batch and hand out its ticket.
+static lc_status submit_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_host,
+                             lc_mode m, cudaStream_t s, bool after_stream, uint64_t* ticket) {
+  const uint64_t t = ctx->next_ticket++;
+  *ticket = t;
+  if (count == 0) return LC_OK;
+  HostSlot* h = &ctx->hslots[0];
+  for (auto& c : ctx->hslots)
+    if (c.ticket < h->ticket) h = &c;  // a free slot (ticket 0) or the oldest batch
+  lc_status st = retire_slot(*h);
+  if (st != LC_OK) return st;
+  st = enqueue_host(ctx, *h, reqs, count, status_host, m, s, after_stream);
+  if (st != LC_OK) {
+    // leave nothing of this batch in flight
+    cudaStreamSynchronize(ctx->copy_in);
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(ctx->copy_out);
+    return st;
+  }
+  h->ticket = t;
+  return LC_OK;
+}
+
+static lc_status wait_host(lc_ctx* ctx, uint64_t ticket) {
+  lc_status st = LC_OK;
+  for (auto& h : ctx->hslots)
+    if (h.ticket && h.ticket <= ticket) {
+      lc_status r = retire_slot(h);
+      if (st == LC_OK) st = r;
+    }
+  return st;
+}
+
+lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_host,
+                            lc_mode m, void* stream) {
+  if (!ctx || (!reqs && count) || (!status_host && count)) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  if (count == 0) return LC_OK;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint64_t t = 0;
+  lc_status st = submit_host(ctx, reqs, count, status_host, m, s, true, &t);
+  if (st != LC_OK) return st;
+  st = wait_host(ctx, t);
+  if (st != LC_OK) return st;
   LC_CUDA(cudaStreamSynchronize(s));
   return LC_OK;
+}
+
+lc_status lc_submit_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_host,
+                               lc_mode m, void* stream, uint64_t* ticket) {
+  if (!ctx || !ticket || (!reqs && count) || (!status_host && count)) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  return submit_host(ctx, reqs, count, status_host, m, static_cast<cudaStream_t>(stream), false, ticket);
+}
+
+lc_status lc_wait_batch_host(lc_ctx* ctx, uint64_t ticket) {
+  if (!ctx || ticket == 0 || ticket >= ctx->next_ticket) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  return wait_host(ctx, ticket);
 }
 
 lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out) {

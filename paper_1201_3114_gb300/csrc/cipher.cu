@@ -253,6 +253,12 @@ struct V1Path {
   }
 };
 
+// v[q] of (v0, v1, v2, v3), q < 4, without indexing a local array.
+__device__ __forceinline__ uint32_t sel4(uint32_t q, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+  const uint32_t lo = (q & 1u) ? v1 : v0, hi = (q & 1u) ? v3 : v2;
+  return (q & 2u) ? hi : lo;
+}
+
 // One trajectory: Eq. 5 plus the part offset b * eta, the warm-up, then the
 // part's body bytes and its tag.  Returns the tag verdict (always true when
 // encrypting).
@@ -284,37 +290,54 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
 
   const uint8_t* src = Mg.in + lo;
   uint8_t* dst = Mg.out + lo;
+  // Head: single bytes until dst is 16-byte aligned.  Body: 16 bytes per
+  // aligned store; the input comes from aligned 16-byte loads, realigned to
+  // the source's offset (any offset, so packed buffers keep the vector path).
+  // Tail: single bytes.
+  const uint64_t head = min((uint64_t)((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u), len);
   uint64_t i = 0;
-  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
-    const uint64_t nv = len >> 4;
-    const uint4* s4 = reinterpret_cast<const uint4*>(src);
-    uint4* d4 = reinterpret_cast<uint4*>(dst);
-    if (nv) {
-      uint4 cur = s4[0];
-      for (uint64_t c = 0; c < nv; c++) {
-        uint4 nxt = cur;
-        if (c + 1 < nv) nxt = s4[c + 1];  // read ahead before the store (in-place safe)
-        // 16 bytes through a rolled loop: the 128-bit input shifts down one
-        // byte per step and each output byte enters at the top.
-        uint32_t i0 = cur.x, i1 = cur.y, i2 = cur.z, i3 = cur.w;
-        uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+  for (; i < head; i++) dst[i] = (uint8_t)t.step(src[i], dec, p, theta);
+  const uint64_t nv = (len - head) >> 4;
+  if (nv) {
+    const uint8_t* s1 = src + head;
+    const uint32_t sa = (uint32_t)(reinterpret_cast<uintptr_t>(s1) & 15u);
+    const uint4* s4 = reinterpret_cast<const uint4*>(s1 - sa);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
+    uint4 cur = s4[0];
+    for (uint64_t c = 0; c < nv; c++) {
+      // Chunk c reads s4[c] and, when sa > 0, s4[c + 1]: an aligned block
+      // that holds at least one byte of this part.  The next block is read
+      // before the store, so in-place operation (sa == 0) stays safe.
+      uint4 nxt = cur;
+      if (c + 1 < nv || sa) nxt = s4[c + 1];
+      // bytes sa .. sa + 15 of cur:nxt
+      const uint32_t q = sa >> 2, sh = (sa & 3u) * 8u;
+      const uint32_t w0 = sel4(q, cur.x, cur.y, cur.z, cur.w);
+      const uint32_t w1 = sel4(q, cur.y, cur.z, cur.w, nxt.x);
+      const uint32_t w2 = sel4(q, cur.z, cur.w, nxt.x, nxt.y);
+      const uint32_t w3 = sel4(q, cur.w, nxt.x, nxt.y, nxt.z);
+      const uint32_t w4 = sel4(q, nxt.x, nxt.y, nxt.z, nxt.w);
+      // 16 bytes through a rolled loop: the 128-bit input shifts down one
+      // byte per step and each output byte enters at the top.
+      uint32_t i0 = __funnelshift_r(w0, w1, sh), i1 = __funnelshift_r(w1, w2, sh);
+      uint32_t i2 = __funnelshift_r(w2, w3, sh), i3 = __funnelshift_r(w3, w4, sh);
+      uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
 #pragma unroll 1
-        for (int j = 0; j < 16; j++) {
-          const uint32_t yb = t.step(i0 & 255u, dec, p, theta);
-          i0 = __funnelshift_r(i0, i1, 8);
-          i1 = __funnelshift_r(i1, i2, 8);
-          i2 = __funnelshift_r(i2, i3, 8);
-          i3 >>= 8;
-          o0 = __funnelshift_r(o0, o1, 8);
-          o1 = __funnelshift_r(o1, o2, 8);
-          o2 = __funnelshift_r(o2, o3, 8);
-          o3 = (o3 >> 8) | (yb << 24);
-        }
-        d4[c] = make_uint4(o0, o1, o2, o3);
-        cur = nxt;
+      for (int j = 0; j < 16; j++) {
+        const uint32_t yb = t.step(i0 & 255u, dec, p, theta);
+        i0 = __funnelshift_r(i0, i1, 8);
+        i1 = __funnelshift_r(i1, i2, 8);
+        i2 = __funnelshift_r(i2, i3, 8);
+        i3 >>= 8;
+        o0 = __funnelshift_r(o0, o1, 8);
+        o1 = __funnelshift_r(o1, o2, 8);
+        o2 = __funnelshift_r(o2, o3, 8);
+        o3 = (o3 >> 8) | (yb << 24);
       }
+      d4[c] = make_uint4(o0, o1, o2, o3);
+      cur = nxt;
     }
-    i = nv << 4;
+    i = head + (nv << 4);
   }
   for (; i < len; i++) dst[i] = (uint8_t)t.step(src[i], dec, p, theta);
 

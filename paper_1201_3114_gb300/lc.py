@@ -20,6 +20,12 @@ LC_OK, LC_ERR_ARG, LC_ERR_PASSWORD, LC_ERR_LENGTH, LC_ERR_INTEGRITY = 0, 1, 2, 3
 LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_NOMEM = 5, 6, 7
 LC_PARALLEL, LC_SEQUENTIAL = 0, 1
 LC_ENCRYPT, LC_DECRYPT = 0, 1
+LC_HOST_INFLIGHT = 2
+
+# objects a submitted host batch reads or writes after the call returns,
+# kept alive until its ticket is waited for: {(ctx, ticket): refs}
+_host_inflight = {}
+_host_lock = threading.Lock()
 
 
 class lc_params(C.Structure):
@@ -130,6 +136,9 @@ _SIGNATURES = {
                                C.c_void_p]),
     "lc_run_batch_host": (C.c_int, [C.c_void_p, C.POINTER(lc_req), C.c_size_t, C.c_void_p,
                                     C.c_int, C.c_void_p]),
+    "lc_submit_batch_host": (C.c_int, [C.c_void_p, C.POINTER(lc_req), C.c_size_t, C.c_void_p,
+                                       C.c_int, C.c_void_p, C.POINTER(C.c_uint64)]),
+    "lc_wait_batch_host": (C.c_int, [C.c_void_p, C.c_uint64]),
     "lc_ctx_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lc_launch)]),
     "lc_ctx_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lc_launch)]),
     "lc_tune": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(lc_launch)]),
@@ -281,6 +290,9 @@ def lc_ctx_create(device: int = 0) -> int:
 
 def lc_ctx_destroy(ctx) -> None:
     load().lc_ctx_destroy(ctx)
+    with _host_lock:
+        for key in [k for k in _host_inflight if k[0] == ctx]:
+            del _host_inflight[key]
 
 
 def lc_ctx_set_params(ctx, p: lc_params) -> int:
@@ -347,6 +359,27 @@ def lc_run_batch_noalloc(batch: Batch, status_dev, mode=LC_PARALLEL, stream=None
 def lc_run_batch_host(ctx, batch: Batch, status_host, mode=LC_PARALLEL, stream=None) -> int:
     return load().lc_run_batch_host(ctx, batch.reqs, batch.count, _ptr(status_host), mode,
                                     _stream(stream))
+
+
+def lc_submit_batch_host(ctx, batch: Batch, status_host, mode=LC_PARALLEL, stream=None):
+    """(status, ticket).  The host buffers of ``batch`` and ``status_host``
+    must stay alive and unchanged until lc_wait_batch_host(ctx, ticket)."""
+    t = C.c_uint64(0)
+    st = load().lc_submit_batch_host(ctx, batch.reqs, batch.count, _ptr(status_host), mode,
+                                     _stream(stream), C.byref(t))
+    if st == LC_OK:
+        with _host_lock:
+            _host_inflight[(ctx, t.value)] = (batch, status_host)
+    return st, t.value
+
+
+def lc_wait_batch_host(ctx, ticket) -> int:
+    st = load().lc_wait_batch_host(ctx, ticket)
+    if st != LC_ERR_ARG:
+        with _host_lock:
+            for key in [k for k in _host_inflight if k[0] == ctx and k[1] <= ticket]:
+                del _host_inflight[key]
+    return st
 
 
 def lc_ctx_get_launch(ctx) -> lc_launch:

@@ -21,6 +21,14 @@ def test_library_exports_every_declared_symbol():
         assert callable(getattr(lc, n)), n
 
 
+def test_binding_constants_match_header():
+    import re
+    text = open(lc.HEADER).read()
+    defs = dict(re.findall(r"#define\s+(LC_[A-Z0-9_]+)\s+(\d+)u?", text))
+    for name in ("LC_STATS_MAX_LAG", "LC_HOST_INFLIGHT"):
+        assert int(defs[name]) == getattr(lc, name), name
+
+
 def test_version_and_status_strings():
     assert lc.lc_version() == 1
     for s in range(8):

@@ -99,7 +99,7 @@ def test_every_password_length(ctx):
 
 
 def test_unaligned_buffers(ctx):
-    # Misaligned input or output pointers take the byte path; results agree.
+    # Misaligned input or output pointers; results agree.
     n = 2 * B + 21
     P = synth.uniform_bytes(44, n)
     pw = b"unaligned-buffers"
@@ -117,6 +117,37 @@ def test_unaligned_buffers(ctx):
         st = lc.lc_decrypt(ctx.handle, pw, dst.data_ptr() + pout, want.size, back.data_ptr() + pin,
                            n, lc.LC_PARALLEL)
         assert st == lc.LC_OK and np.array_equal(host(back)[pin:pin + n], P)
+
+
+@pytest.mark.parametrize("mode", [lc.LC_PARALLEL, lc.LC_SEQUENTIAL])
+def test_every_alignment_pair(ctx, mode):
+    # Every (source, destination) offset modulo 16, both directions, in one
+    # batch: head bytes, the realigned 16-byte body and the tail all vary.
+    reqs, want_out, outs = [], [], []
+    keep = []
+    k = 0
+    for pin in range(16):
+        for pout in range(16):
+            n = B + 37 + (k % 23) if mode == lc.LC_PARALLEL else 300 + k % 41
+            pw = synth.password(synth.subseed(46, k), 1 + k % 32)
+            P = synth.uniform_bytes(synth.subseed(47, k), n)
+            Cw = O.encrypt(pw, P, mode)
+            for d, x, y in ((0, P, Cw), (1, Cw, P)):
+                src = torch.zeros(x.size + 32, dtype=torch.uint8, device="cuda")
+                dst = torch.full((y.size + 32,), 0x5A, dtype=torch.uint8, device="cuda")
+                src[pin:pin + x.size] = dev(x)
+                reqs.append((pw, d, src.data_ptr() + pin, x.size, dst.data_ptr() + pout, y.size))
+                want_out.append((pout, y))
+                outs.append(dst)
+                keep.append(src)
+            k += 1
+    st = torch.full((len(reqs),), -1, dtype=torch.int32, device="cuda")
+    lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(reqs), st, mode))
+    assert (host(st) == 0).all()
+    for i, ((pout, y), dst) in enumerate(zip(want_out, outs)):
+        got = host(dst)
+        assert np.array_equal(got[pout:pout + y.size], y), i
+        assert (got[:pout] == 0x5A).all() and (got[pout + y.size:] == 0x5A).all(), i
 
 
 def test_in_place(ctx):
@@ -475,8 +506,8 @@ def test_n_it_steps_per_byte_profile():
 
 
 def test_host_buffer_batch_pageable_and_scattered(ctx):
-    # Pageable numpy buffers (one per request, not contiguous) take the
-    # staging path; page-locked ones the zero-copy path.  Both equal the oracle.
+    # Pageable numpy buffers (one per request, not contiguous) and
+    # page-locked ones both equal the oracle.
     msgs = _mixed_batch(24, 63, max_size=20000)
     ins, outs, want = [], [], []
     for pw, d, P in msgs:
@@ -503,3 +534,69 @@ def test_host_buffer_batch_pageable_and_scattered(ctx):
             assert st[i] == lc.LC_ERR_INTEGRITY and not y.numpy().any()
         else:
             assert st[i] == 0 and np.array_equal(y.numpy()[:w.size], w), i
+
+
+def _host_batch(seed, count, pinned=True, tamper=False):
+    """(Batch, status array, output buffers, expected outputs, refs)."""
+    msgs = _mixed_batch(count, seed, max_size=3 * B + 100)
+    ins, want = [], []
+    for pw, d, P in msgs:
+        ct = O.encrypt(pw, P)
+        ins.append(P if d == 0 else ct.copy())
+        want.append(ct if d == 0 else P)
+    bad = None
+    if tamper:
+        bad = next(i for i, (_, d, P) in enumerate(msgs) if d == 1 and P.size > 0)
+        ins[bad][0] ^= 1
+    if pinned:
+        hin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in ins]
+        hout = [torch.full((max(1, w.size),), 0xAA, dtype=torch.uint8).pin_memory() for w in want]
+        items = [(pw, d, x, x.numel(), y, w.size) for (pw, d, _), x, y, w in zip(msgs, hin, hout, want)]
+        outs = [y.numpy() for y in hout]
+    else:
+        hin = [np.ascontiguousarray(x) for x in ins]
+        outs = [np.full(max(1, w.size), 0xAA, dtype=np.uint8) for w in want]
+        items = [(pw, d, x, x.size, y, w.size) for (pw, d, _), x, y, w in zip(msgs, hin, outs, want)]
+    st = np.full(len(items), -1, dtype=np.int32)
+    return lc.Batch(items), st, outs, want, bad, (hin, outs)
+
+
+def _check_host_batch(st, outs, want, bad):
+    for i, (y, w) in enumerate(zip(outs, want)):
+        if i == bad:
+            assert st[i] == lc.LC_ERR_INTEGRITY and not y[:w.size].any(), i
+        else:
+            assert st[i] == lc.LC_OK and np.array_equal(y[:w.size], w), i
+
+
+def test_submitted_host_batches_overlap_and_match_oracle(ctx):
+    h = ctx.handle
+    assert lc.lc_wait_batch_host(h, 0) == lc.LC_ERR_ARG
+    batches = [_host_batch(900 + k, 12 + 3 * k, pinned=(k != 3), tamper=(k == 1)) for k in range(6)]
+    tickets = []
+    for k, (bt, st, outs, want, bad, refs) in enumerate(batches):
+        rc, t = lc.lc_submit_batch_host(h, bt, st)
+        assert rc == lc.LC_OK and t > 0
+        tickets.append(t)
+        if k == 2:
+            # a synchronous host batch and a device batch between submissions
+            sb, sst, souts, swant, sbad, _ = _host_batch(950, 9)
+            lc.check(lc.lc_run_batch_host(h, sb, sst))
+            _check_host_batch(sst, souts, swant, sbad)
+            gpu_out = gpu_encrypt(ctx, b"between", synth.uniform_bytes(951, 5 * B + 3))
+            assert np.array_equal(gpu_out, O.encrypt(b"between", synth.uniform_bytes(951, 5 * B + 3)))
+    assert tickets == sorted(tickets) and len(set(tickets)) == len(tickets)
+    assert lc.lc_wait_batch_host(h, tickets[-1] + 1) == lc.LC_ERR_ARG
+    # waiting for the fifth ticket completes every earlier batch too
+    assert lc.lc_wait_batch_host(h, tickets[4]) == lc.LC_OK
+    for k in range(5):
+        _, st, outs, want, bad, _ = batches[k]
+        _check_host_batch(st, outs, want, bad)
+    assert lc.lc_wait_batch_host(h, tickets[5]) == lc.LC_OK
+    _, st, outs, want, bad, _ = batches[5]
+    _check_host_batch(st, outs, want, bad)
+    # waiting again is a no-op; an empty batch gets a completed ticket
+    assert lc.lc_wait_batch_host(h, tickets[2]) == lc.LC_OK
+    rc, t = lc.lc_submit_batch_host(h, lc.Batch([]), np.zeros(1, np.int32))
+    assert rc == lc.LC_OK and t > tickets[-1]
+    assert lc.lc_wait_batch_host(h, t) == lc.LC_OK
