@@ -195,6 +195,15 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def measured_peaks():
+    """The measured HBM copy and bf16 GEMM peaks of this GPU model, if recorded."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def committed_traffic():
     """DRAM traffic per launch from the committed ncu summary, if it was taken
     on the current kernel sources."""
@@ -377,6 +386,99 @@ def profile_case(args):
     return 0
 
 
+def next_rows(args):
+    """Throughput of the widened rows: batched sequential mode (one message
+    per thread), the S = 3000 steps-per-byte profile, the delta t = 0.027
+    profile and the ciphertext statistics kernel.  One JSON line."""
+    import torch
+    from paper_1201_3114_gb300 import lc, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {"case": "next_rows", "source_hash": source_hash()}
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def check_status(st):
+        bad = int((st != 0).sum())
+        if bad:
+            raise SystemExit("next_rows: %d requests failed" % bad)
+
+    # batched sequential mode: one 16 KiB message per resident thread of
+    # the persistent grid (3 CTAs x 256 threads per SM), against the same
+    # messages in parallel mode (4 parts each)
+    with lc.Context(0) as ctx:
+        cnt, sz = sms * 768, 16384
+        arena = torch.empty(cnt * sz, dtype=torch.uint8, device="cuda")
+        lc.check(lc.lc_synth_uniform(arena, cnt * sz, synth.config_seed(3) + 17, 0, stream))
+        res = {}
+        for mode, name in ((lc.LC_SEQUENTIAL, "sequential"), (lc.LC_PARALLEL, "parallel")):
+            clen = ctx.ciphertext_len(sz, mode)
+            outb = torch.empty(cnt * clen, dtype=torch.uint8, device="cuda")
+            pws = [synth.password(synth.subseed(synth.config_seed(3), 5000 + i), 16) for i in range(256)]
+            items = [(pws[i % 256], lc.LC_ENCRYPT, arena.data_ptr() + i * sz, sz,
+                      outb.data_ptr() + i * clen, clen) for i in range(cnt)]
+            b = lc.Batch(items)
+            st = torch.full((cnt,), -1, dtype=torch.int32, device="cuda")
+            ms = timed(lambda: lc.check(lc.lc_run_batch(ctx.handle, b, st, mode, stream)), args.steps)
+            check_status(st)
+            res[name] = {"ms_per_batch": ms, "GBps": cnt * sz / ms / 1e6}
+            del outb
+        out["batched_sequential"] = {
+            "messages": cnt, "message_bytes": sz, **{k: v for k, v in res.items()},
+            "sequential_over_parallel": res["sequential"]["GBps"] / res["parallel"]["GBps"],
+            "note": "sequential: one trajectory of 16384 + 8 steps and one warm-up per message; "
+                    "parallel: 4 parts, each with its own warm-up"}
+        del arena
+
+    # the S = 3000 profile (one Euler step count per byte read as n_it):
+    # 64-byte parts, one part per resident thread
+    with lc.Context(0, lc.params(steps_per_byte=3000, block_len=64)) as c:
+        n = sms * 768 * 64
+        P = torch.empty(n, dtype=torch.uint8, device="cuda")
+        lc.check(lc.lc_synth_uniform(P, n, synth.config_seed(3) + 18, 0, stream))
+        Cb = torch.empty(c.ciphertext_len(n), dtype=torch.uint8, device="cuda")
+        ms = timed(lambda: lc.check(lc.lc_encrypt(c.handle, b"n_it-profile-pw", P, n, Cb, Cb.numel(),
+                                                  lc.LC_PARALLEL, stream)), 1)
+        parts = n // 64
+        steps = parts * (3000 + (64 + 8) * 3000)  # warm-up, then S steps per body and tag byte
+        out["s3000_profile"] = {"bytes": n, "block_len": 64, "ms": ms, "MBps": n / ms / 1e3,
+                                "euler_steps_per_s": steps / (ms * 1e-3)}
+
+    # the delta t = 0.027 profile (the trajectory leaves the attractor and
+    # saturates; every emulated operation then takes its hardware fallback)
+    with lc.Context(0, lc.params(dt=0.027)) as c:
+        n = 256 << 20
+        P = torch.empty(n, dtype=torch.uint8, device="cuda")
+        lc.check(lc.lc_synth_uniform(P, n, synth.config_seed(3) + 19, 0, stream))
+        Cb = torch.empty(c.ciphertext_len(n), dtype=torch.uint8, device="cuda")
+        ms = timed(lambda: lc.check(lc.lc_encrypt(c.handle, b"dt-0.027-profile", P, n, Cb, Cb.numel(),
+                                                  lc.LC_PARALLEL, stream)), 2)
+        out["dt0027_profile"] = {"bytes": n, "ms": ms, "GBps": n / ms / 1e6}
+
+    # ciphertext statistics (histogram, sums, lagged products) over 1 GiB
+    with lc.Context(0) as ctx:
+        n = 1 << 30
+        P = torch.empty(n, dtype=torch.uint8, device="cuda")
+        lc.check(lc.lc_synth_uniform(P, n, synth.config_seed(3) + 20, 0, stream))
+        ms = timed(lambda: lc.lc_byte_stats(ctx.handle, P, n, 8, stream), args.steps)
+        peak = measured_peaks().get("hbm_gbs")
+        out["stats_1GiB"] = {"ms": ms, "GBps": n / ms / 1e6, "hbm_peak_GBps": peak,
+                             "frac_of_measured_hbm": (n / ms / 1e6) / peak if peak else None}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,6 +497,9 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0, metavar="MIB",
                     help="only time one MIB-MiB parallel-mode encryption per step (a small "
                          "case for ncu captures); prints a short JSON line")
+    ap.add_argument("--next-rows", action="store_true",
+                    help="only time the widened rows (batched sequential mode, the S = 3000 "
+                         "and delta t = 0.027 profiles, the statistics kernel); one JSON line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -402,6 +507,8 @@ def main():
         return reference_arm(args)
     if args.profile_case:
         return profile_case(args)
+    if args.next_rows:
+        return next_rows(args)
 
     import torch
     from paper_1201_3114_gb300 import lc
