@@ -214,12 +214,16 @@ lc_status lc_wait_batch_host(lc_ctx* ctx, uint64_t ticket);
  * variant that keeps all binary64 work on the FP64 pipe (lower latency
  * while the GPU is far from full); larger batches run the variant that
  * moves the multiplies to the integer pipes (higher throughput).  0 = auto
- * (192 parts per SM).  The shape never changes results. */
+ * (192 parts per SM).  host_chunk_mib: a host-buffer batch whose inputs
+ * exceed this many MiB is cut into up to 4 chunks of whole requests, so
+ * that one chunk's copies overlap another's kernel (0 = 4096 MiB).  None of
+ * these changes results. */
 typedef struct {
   uint32_t threads_per_cta;
   uint32_t ctas_per_sm;
   uint32_t smem_staging;
   uint32_t small_batch_rows;
+  uint32_t host_chunk_mib;
 } lc_launch;
 
 lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out);

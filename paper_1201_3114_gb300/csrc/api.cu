@@ -101,7 +101,7 @@ struct lc_ctx {
     int grid = 0;
   } graphs[kNumVariants];
 
-  lc_launch launch{256, 0, 0, 0};
+  lc_launch launch{256, 0, 0, 0, 0};
 
   std::unordered_map<std::string, HostKey> keys;
 
@@ -800,7 +800,8 @@ static lc_status enqueue_host(lc_ctx* ctx, HostSlot& h, const lc_req* reqs, size
   // 22 GB/s as one launch.  Overlap between batches comes from the slots.
   size_t total_in = 0;
   for (size_t i = 0; i < count; i++) total_in += reqs[i].in_len;
-  const size_t K = std::max<size_t>(1, std::min<size_t>(4, total_in / ((size_t)4 << 30)));
+  const size_t chunk = (size_t)(ctx->launch.host_chunk_mib ? ctx->launch.host_chunk_mib : 4096) << 20;
+  const size_t K = std::max<size_t>(1, std::min<size_t>(4, total_in / chunk));
   std::vector<size_t> bound{0};
   {
     size_t acc = 0, next = 1;
@@ -981,7 +982,7 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
     std::vector<uint32_t> cands = {0};
     for (uint32_t c = 1; c < (uint32_t)maxc; c *= 2) cands.push_back(c);
     for (uint32_t c : cands) {
-      lc_launch l{tpc, c, 0, saved.small_batch_rows};
+      lc_launch l{tpc, c, 0, saved.small_batch_rows, saved.host_chunk_mib};
       ctx->launch = l;
       invalidate_graphs(ctx);
       int32_t* stat = nullptr;

@@ -62,6 +62,7 @@ class lc_launch(C.Structure):
         ("ctas_per_sm", C.c_uint32),
         ("smem_staging", C.c_uint32),
         ("small_batch_rows", C.c_uint32),
+        ("host_chunk_mib", C.c_uint32),
     ]
 
 
@@ -389,8 +390,8 @@ def lc_ctx_get_launch(ctx) -> lc_launch:
 
 
 def lc_ctx_set_launch(ctx, threads_per_cta=256, ctas_per_sm=0, smem_staging=0,
-                      small_batch_rows=0) -> int:
-    l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, small_batch_rows)
+                      small_batch_rows=0, host_chunk_mib=0) -> int:
+    l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, small_batch_rows, host_chunk_mib)
     return load().lc_ctx_set_launch(ctx, C.byref(l))
 
 

@@ -600,3 +600,52 @@ def test_submitted_host_batches_overlap_and_match_oracle(ctx):
     rc, t = lc.lc_submit_batch_host(h, lc.Batch([]), np.zeros(1, np.int32))
     assert rc == lc.LC_OK and t > tickets[-1]
     assert lc.lc_wait_batch_host(h, t) == lc.LC_OK
+
+
+def test_chunked_host_batch(ctx):
+    # A host-buffer batch larger than host_chunk_mib is cut into up to 4
+    # chunks whose copies overlap the other chunks' kernels; results are
+    # those of the oracle, in one synchronous call and in pipelined submits.
+    rng = np.random.default_rng(71)
+    msgs = []
+    for m in range(48):
+        n = int(rng.integers(1, 200 * 1024))
+        pw = synth.password(synth.subseed(72, m), 8 + m % 25)
+        P = synth.uniform_bytes(synth.subseed(73, m), n)
+        msgs.append((pw, m % 2, P))
+    ins, want = [], []
+    for pw, d, P in msgs:
+        ct = O.encrypt(pw, P)
+        ins.append(P if d == 0 else ct)
+        want.append(ct if d == 0 else P)
+    assert sum(x.size for x in ins) > 4 << 20
+    hin = torch.empty(sum(x.size for x in ins), dtype=torch.uint8).pin_memory()
+    a = 0
+    offs = []
+    for x in ins:
+        hin[a:a + x.size] = torch.from_numpy(x)
+        offs.append(a)
+        a += x.size
+    try:
+        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, 0, 1) == lc.LC_OK
+        for rep in range(3):
+            hout = torch.full((sum(w.size for w in want),), 0x33, dtype=torch.uint8).pin_memory()
+            items, b_ = [], 0
+            for (pw, d, _), x, o, w in zip(msgs, ins, offs, want):
+                items.append((pw, d, hin.data_ptr() + o, x.size, hout.data_ptr() + b_, w.size))
+                b_ += w.size
+            st = np.full(len(items), -1, dtype=np.int32)
+            if rep == 0:
+                lc.check(lc.lc_run_batch_host(ctx.handle, lc.Batch(items), st))
+            else:
+                rc, t = lc.lc_submit_batch_host(ctx.handle, lc.Batch(items), st)
+                assert rc == lc.LC_OK
+                assert lc.lc_wait_batch_host(ctx.handle, t) == lc.LC_OK
+            assert (st == 0).all(), rep
+            got = hout.numpy()
+            b_ = 0
+            for w in want:
+                assert np.array_equal(got[b_:b_ + w.size], w), rep
+                b_ += w.size
+    finally:
+        lc.lc_ctx_set_launch(ctx.handle, 256, 0)
