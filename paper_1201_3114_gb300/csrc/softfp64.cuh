@@ -147,48 +147,50 @@ __device__ __forceinline__ double dmul(double a, double b) {
 
 // RN(a + b) for two normal operands (either sign) with a normal result.
 // Subtraction of operands whose exponents differ by at most one can cancel
-// many leading bits; that case is rare in the cipher and goes to the
-// hardware.  Otherwise the sum needs at most a one-bit renormalisation, and
-// three extra bits (guard, round, sticky) give the correctly rounded result.
+// many leading bits; that case, and exponent gaps of 32 or more (where b
+// only affects the rounding), are rare in the cipher and go to the hardware.
+//
+// The significands are placed at bits 62..10 of 64-bit words, leaving ten
+// bits below the last place.  The smaller operand is shifted right by the
+// gap d < 32 and any bits shifted out are folded into its bit 0 (sticky):
+// with ten spare bits the folded value and the exact one round the same
+// way.  The sum then has its leading bit at 63, 62 or 61, so rounding keeps
+// the 53 bits from the leading one: round-half-even by adding half an ulp
+// minus one plus the last kept bit, then truncating.
 __device__ __forceinline__ double dadd(double a, double b) {
-  uint32_t xh = hi32(a), xl = lo32(a), yh = hi32(b), yl = lo32(b);
-  // order by magnitude: |x| >= |y|
-  const uint32_t mxh = xh & 0x7FFFFFFFu, myh = yh & 0x7FFFFFFFu;
-  const bool swap = (mxh < myh) || (mxh == myh && xl < yl);
-  const uint32_t th = swap ? yh : xh, tl = swap ? yl : xl;
-  yh = swap ? xh : yh;
-  yl = swap ? xl : yl;
-  xh = th;
-  xl = tl;
-  const uint32_t ex = (xh >> 20) & 0x7FFu, ey = (yh >> 20) & 0x7FFu;
+  const uint32_t ah = hi32(a), al = lo32(a), bh = hi32(b), bl = lo32(b);
+  // order by magnitude (high words suffice: equal high words mean equal
+  // exponents, where the order does not matter or the hardware is used)
+  const uint32_t mah = ah & 0x7FFFFFFFu, mbh = bh & 0x7FFFFFFFu;
+  const bool sw = mah < mbh;
+  const uint32_t xh = sw ? bh : ah, xl = sw ? bl : al;
+  const uint32_t yh = sw ? ah : bh, yl = sw ? al : bl;
+  const uint32_t ex = max(mah, mbh) >> 20, ey = min(mah, mbh) >> 20;
   const uint32_t d = ex - ey;
-  const bool sub = ((xh ^ yh) & 0x80000000u) != 0u;
-  if (ey == 0u || ex - 60u > 1985u || (sub && d <= 1u)) return hw_add(a, b);
-  // significands with three extra low bits: [2^55, 2^56)
-  const uint64_t Mx = (((uint64_t)((xh & 0xFFFFFu) | 0x100000u) << 32) | xl) << 3;
-  const uint64_t My0 = (((uint64_t)((yh & 0xFFFFFu) | 0x100000u) << 32) | yl) << 3;
-  // align: My >> d, the bits shifted out folded into a sticky bit
-  const uint32_t dc = d < 63u ? d : 63u;
-  uint64_t My = My0 >> dc;
-  My |= ((My0 << (63u - dc)) << 1) != 0ull ? 1ull : 0ull;
-  uint64_t R;
-  uint32_t E = ex;
-  if (!sub) {
-    R = Mx + My;  // < 2^57
-    const uint32_t c = (uint32_t)(R >> 56);
-    R = c ? ((R >> 1) | (R & 1ull)) : R;
-    E += c;
-  } else {
-    R = Mx - My;  // in [2^54, 2^56) since d >= 2
-    const uint32_t n = 1u - (uint32_t)((R >> 55) & 1ull);
-    R <<= n;
-    E -= n;
-  }
-  // R in [2^55, 2^56): 53 bits and 3 guard/round/sticky bits
-  uint64_t q = R >> 3;
-  const uint32_t g = (uint32_t)R & 7u;
-  q += (g > 4u || (g == 4u && (q & 1ull))) ? 1ull : 0ull;
-  return from_bits(((uint64_t)(xh & 0x80000000u) << 32) | ((((uint64_t)E - 1ull) << 52) + q));
+  const uint32_t sub = (ah ^ bh) >> 31;
+  // fast path: y normal, no overflow past the top binade, gap < 32, and a
+  // subtraction only with gap >= 2 (at most one leading bit cancels)
+  if (ey == 0u || ex > 2045u || d > 31u || (sub != 0u && d < 2u)) return hw_add(a, b);
+  const uint32_t xm = (xh & 0xFFFFFu) | 0x100000u, ym = (yh & 0xFFFFFu) | 0x100000u;
+  const uint32_t X1 = __funnelshift_l(xl, xm, 10), X0 = xl << 10;
+  const uint32_t Y1 = __funnelshift_l(yl, ym, 10), Y0 = yl << 10;
+  const uint32_t s0 = __funnelshift_r(Y0, Y1, d), s1 = Y1 >> d;
+  const uint32_t lost = Y0 & ((1u << d) - 1u);
+  // X + Y, or X - Y as X + ~Y + 1
+  const uint32_t m = 0u - sub;
+  const uint32_t t0 = (s0 | (lost != 0u ? 1u : 0u)) ^ m, t1 = s1 ^ m;
+  const uint64_t R = ((((uint64_t)X1 << 32) | X0) + (((uint64_t)t1 << 32) | t0)) + sub;
+  // leading bit at 63 - lz; the result's biased exponent is ex + 1 - lz
+  const uint32_t lz = __clz((uint32_t)(R >> 32));
+  const uint32_t rp = 11u - lz;  // bits below the last kept place
+  const uint32_t last = ((uint32_t)R >> rp) & 1u;
+  const uint64_t T = R + ((1u << (rp - 1u)) - 1u + last);
+  const uint32_t T1 = (uint32_t)(T >> 32), T0 = (uint32_t)T;
+  const uint32_t q0 = __funnelshift_r(T0, T1, rp), q1 = T1 >> rp;
+  // q has its hidden bit at 2^52 (2^53 after a rounding carry), which
+  // supplies the last 1 of the exponent field (or steps to the next binade)
+  const uint32_t hi = (xh & 0x80000000u) + ((ex - lz) << 20) + q1;
+  return pack(hi, q0);
 }
 
 __device__ __forceinline__ double dsub(double a, double b) { return dadd(a, -b); }
