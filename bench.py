@@ -487,7 +487,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--messages", type=int, default=4096)
     ap.add_argument("--per-message-sample", type=int, default=256)
-    ap.add_argument("--cpu-sample-mb", type=int, default=96)
+    ap.add_argument("--cpu-sample-mb", type=int, default=512)
     ap.add_argument("--ref-sample-mb", type=int, default=96)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
@@ -731,7 +731,8 @@ def main():
         b_cpu, s_cpu = run_oracle_sample(spec, plan, threads)
         cpu = {"value": b_cpu / s_cpu / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%.0f MiB: the first parts of every message in proportion to its size"
-                         % (b_cpu / 2 ** 20)}
+                         % (b_cpu / 2 ** 20),
+               "wall_s": s_cpu, "cpu_s_max": s_cpu * threads}
 
     if served and pm:
         for rec in served.values():
