@@ -21,7 +21,11 @@
  *   - Errors are returned as lc_status, never thrown.  There is no CPU
  *     fallback: without a usable CUDA device every compute call returns
  *     LC_ERR_CUDA.
- *   - One lc_ctx must not be used by two host threads at once.
+ *   - One lc_ctx must not be used by two host threads at once.  One thread
+ *     may pass different streams to one context: a context's batches share
+ *     its workspace, so each waits on the GPU for the context's previous
+ *     batch when the stream changes.  Independent streams that should run
+ *     concurrently need a context each.
  *   - In-place operation (input == output) is allowed: every byte is read by
  *     the same thread before it is written.  Partly overlapping input and
  *     output ranges give LC_ERR_ARG.

@@ -87,6 +87,8 @@ struct lc_ctx {
   cudaStream_t copy_in = nullptr, copy_out = nullptr;  // host-buffer batch copies
   HostSlot hslots[LC_HOST_INFLIGHT];
   uint64_t next_ticket = 1;
+  cudaEvent_t last_batch_done = nullptr;  // the context's latest batch has finished
+  cudaStream_t last_batch_stream = nullptr;
 
   Staging staging[2];
   int slot = 0;
@@ -475,6 +477,11 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   w += nrows * sizeof(DevRow);
   if (count) memcpy(w, ctx->h_init.data(), count * sizeof(int32_t));
 
+  // Every batch of a context uses the same workspace: when the caller
+  // switches streams, this batch's upload waits on the GPU for the previous
+  // batch (its kernels read the workspace until they finish).
+  if (ctx->last_batch_done && ctx->last_batch_stream != s)
+    LC_CUDA(cudaStreamWaitEvent(s, ctx->last_batch_done, 0));
   LC_CUDA(cudaMemcpyAsync(ctx->ws_dev, sg.host, bytes, cudaMemcpyHostToDevice, s));
   LC_CUDA(cudaEventRecord(sg.done, s));
   sg.used = true;
@@ -493,6 +500,10 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   }
   LC_CUDA(cudaGraphLaunch(G.exec, s));
   ctx->launches += 2;  // cipher kernel + finalize kernel
+  if (!ctx->last_batch_done)
+    LC_CUDA(cudaEventCreateWithFlags(&ctx->last_batch_done, cudaEventDisableTiming));
+  LC_CUDA(cudaEventRecord(ctx->last_batch_done, s));
+  ctx->last_batch_stream = s;
   return LC_OK;
 }
 
@@ -621,6 +632,7 @@ void lc_ctx_destroy(lc_ctx* ctx) {
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
   if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+  if (ctx->last_batch_done) cudaEventDestroy(ctx->last_batch_done);
   delete ctx;
 }
 

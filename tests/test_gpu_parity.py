@@ -649,3 +649,31 @@ def test_chunked_host_batch(ctx):
                 b_ += w.size
     finally:
         lc.lc_ctx_set_launch(ctx.handle, 256, 0)
+
+
+def test_one_context_two_streams(ctx):
+    # Batches of one context issued on two streams without host
+    # synchronisation: each waits for the previous one on the GPU, because
+    # they share the context's workspace.  Every result equals the oracle.
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    jobs = []
+    for k in range(6):
+        msgs = _mixed_batch(40, 300 + k, max_size=6 * B)
+        ins, want = [], []
+        for pw, d, P in msgs:
+            ct = O.encrypt(pw, P)
+            ins.append(dev(P if d == 0 else ct))
+            want.append(ct if d == 0 else P)
+        outs = [torch.full((max(1, w.size),), 0x77, dtype=torch.uint8, device="cuda") for w in want]
+        items = [(pw, d, x, x.numel(), y, w.size) for (pw, d, _), x, y, w in zip(msgs, ins, outs, want)]
+        st = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+        jobs.append((lc.Batch(items), st, ins, outs, want))
+    torch.cuda.synchronize()
+    for k, (b, st, _, _, _) in enumerate(jobs):
+        strm = s1 if k % 2 == 0 else s2
+        lc.check(lc.lc_run_batch(ctx.handle, b, st, lc.LC_PARALLEL, strm))
+    torch.cuda.synchronize()
+    for k, (_, st, _, outs, want) in enumerate(jobs):
+        assert (host(st) == 0).all(), k
+        for y, w in zip(outs, want):
+            assert np.array_equal(host(y)[:w.size], w), k
