@@ -224,6 +224,32 @@ def test_byte_map_is_caesar_and_invertible():
                 assert O.decode_byte(x, r1, r2) == (x - pi) % 256
 
 
+def _byte_map_slice(r2):
+    """Every (x, R1) for one R2: mismatches against the Caesar cipher and
+    against D(E(x)) = x (worker of the exhaustive test)."""
+    import oracle as Ow
+    lib = Ow.lib()
+    enc, dec = lib.lco_encode_byte, lib.lco_decode_byte
+    bad = 0
+    for r1 in range(256):
+        pi = r1 + r2
+        for x in range(256):
+            y = enc(x, r1, r2)
+            if y != (x + pi) % 256 or dec(y, r1, r2) != x or dec(x, r1, r2) != (x - pi) % 256:
+                bad += 1
+    return bad
+
+
+def test_byte_map_exhaustive():
+    # Eqs. 9-10 over all 256^3 (x, R1, R2): the Caesar cipher of Sec. 1 with
+    # key R1 + R2, and decryption inverts encryption (the reversibility of
+    # the mod stated in Sec. 3.2).  16.7 million cases on a spawn pool.
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(8, os.cpu_count() or 1)) as pool:
+        assert sum(pool.map(_byte_map_slice, range(256), chunksize=8)) == 0
+
+
 # --------------------------------------------------------------------------
 # Sec. 3.2 Steps 1-3 in special cases with frozen dynamics
 # --------------------------------------------------------------------------
