@@ -733,6 +733,11 @@ def main():
                "sample": "%.0f MiB: the first parts of every message in proportion to its size"
                          % (b_cpu / 2 ** 20),
                "wall_s": s_cpu, "cpu_s_max": s_cpu * threads}
+        # the same oracle on one core, on a smaller sample of the same kind
+        plan1 = oracle_sample_plan(spec, max(1, args.cpu_sample_mb // 32) << 20)
+        b1, s1 = run_oracle_sample(spec, plan1, 1)
+        cpu["single_core"] = {"value": b1 / s1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": "%.0f MiB" % (b1 / 2 ** 20), "wall_s": s1}
 
     if served and pm:
         for rec in served.values():
