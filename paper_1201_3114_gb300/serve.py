@@ -111,12 +111,14 @@ class Workload:
         return bytes(self.pw_chars[i, :self.pw_len[i]])
 
 
-class Server:
-    """Continuous-batching request loop over ``streams`` CUDA streams."""
+class CudaBackend:
+    """The device side of the serving loop: one lc_ctx, CUDA stream and
+    status buffer per stream slot, the device arena (admission budget) and
+    the device-resident plaintext pool.  Every operation the loop needs from
+    the device goes through these methods."""
 
     def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
-                 max_batch_bytes=256 << 20, max_batch_requests=8192, replay_cap_bytes=None,
-                 seed=0x5E4E):
+                 max_batch_requests=8192, seed=0x5E4E):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -129,28 +131,30 @@ class Server:
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.arena = Arena(budget_bytes, self.device)
         self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
+        self.pool_base = self.pool.data_ptr()
+        self.pool_bytes = pool_bytes
         lc.check(lc.lc_synth_uniform(self.pool, pool_bytes, seed, 0, self.streams[0]))
-        self.max_batch_bytes = max_batch_bytes
-        self.max_batch_requests = max_batch_requests
-        self.replay_cap = replay_cap_bytes if replay_cap_bytes is not None else budget_bytes // 4
         self.status_dev = [torch.zeros(max_batch_requests, dtype=torch.int32, device=self.device)
                            for _ in range(streams)]
         self.status_host = [torch.zeros(max_batch_requests, dtype=torch.int32).pin_memory()
                             for _ in range(streams)]
-        self.reqs = [np.zeros(max_batch_requests, dtype=REQ_DTYPE) for _ in range(streams)]
         torch.cuda.synchronize()
         self.warmup()
+
+    @property
+    def nstreams(self):
+        return len(self.streams)
 
     def warmup(self, nbytes=32 << 20):
         """Run one batch per stream before serving, so that graph capture and
         workspace growth do not land on the first requests."""
         torch = self.torch
-        n = min(nbytes, self.pool.numel())
+        n = min(nbytes, self.pool_bytes)
         out = self.arena.alloc(ct_len(n))
         try:
             for s, c in enumerate(self.ctxs):
                 with torch.cuda.stream(self.streams[s]):
-                    lc.check(lc.lc_encrypt(c.handle, b"warm-up-password", self.pool.data_ptr(), n,
+                    lc.check(lc.lc_encrypt(c.handle, b"warm-up-password", self.pool_base, n,
                                            self.arena.base + out[0], ct_len(n), lc.LC_PARALLEL,
                                            self.streams[s]), "warm-up")
                 torch.cuda.synchronize()
@@ -161,18 +165,105 @@ class Server:
         for c in self.ctxs:
             c.close()
 
+    def start(self):
+        """Mark time zero of a run (host clock and device clock)."""
+        torch = self.torch
+        self.base = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        self.base.record(self.streams[0])
+        torch.cuda.synchronize()
+        self.t0 = time.perf_counter()
+
+    def clock(self):
+        """Seconds since start()."""
+        return time.perf_counter() - self.t0
+
+    def launch(self, s, reqs, count):
+        """Run requests reqs[:count] as one batch on stream slot s; returns a
+        completion token."""
+        torch = self.torch
+        st = self.streams[s]
+        ptr = reqs.ctypes.data_as(C.POINTER(lc.lc_req))
+        rc = lc.load().lc_run_batch(self.ctxs[s].handle, ptr, count, self.status_dev[s].data_ptr(),
+                                    lc.LC_PARALLEL, st.cuda_stream)
+        lc.check(rc, "lc_run_batch")
+        with torch.cuda.stream(st):
+            self.status_host[s][:count].copy_(self.status_dev[s][:count], non_blocking=True)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(st)
+        return ev
+
+    def done(self, token):
+        return token.query()
+
+    def finish_ms(self, token):
+        """Device time of the batch's completion, in ms since start()."""
+        return self.base.elapsed_time(token)
+
+    def statuses(self, s, count):
+        return self.status_host[s].numpy()[:count].copy()
+
+    def tamper_copy(self, s, dst, src, nbytes, pos):
+        """dst <- src (arena blocks, nbytes), then flip byte pos, on slot s."""
+        torch = self.torch
+        v = self.arena.view(dst, nbytes)
+        with torch.cuda.stream(self.streams[s]):
+            v.copy_(self.arena.view(src, nbytes))
+            v[pos:pos + 1].bitwise_xor_(0x5A)
+
+    def read(self, blk, n):
+        """Host copy of n bytes of an arena block (after its batch completed)."""
+        return self.arena.view(blk, n).cpu().numpy()
+
+    def equals_pool(self, blk, n, off):
+        """Whether n bytes of an arena block equal the pool at off (on the device)."""
+        return bool(self.torch.equal(self.arena.view(blk, n), self.pool[off:off + n]))
+
+    def sync(self):
+        self.torch.cuda.synchronize()
+
+    def launch_count(self):
+        return sum(lc.lc_ctx_launch_count(c.handle) for c in self.ctxs)
+
+
+class Server:
+    """Continuous-batching request loop over the backend's stream slots (a
+    CudaBackend unless another backend is given)."""
+
+    def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
+                 max_batch_bytes=256 << 20, max_batch_requests=8192, replay_cap_bytes=None,
+                 seed=0x5E4E, backend=None):
+        self.be = backend if backend is not None else CudaBackend(
+            device, streams, budget_bytes, pool_bytes, max_batch_requests, seed)
+        self.arena = self.be.arena
+        self.max_batch_bytes = max_batch_bytes
+        self.max_batch_requests = max_batch_requests
+        self.replay_cap = replay_cap_bytes if replay_cap_bytes is not None else self.arena.cap // 4
+        self.reqs = [np.zeros(max_batch_requests, dtype=REQ_DTYPE) for _ in range(self.be.nstreams)]
+
+    def close(self):
+        self.be.close()
+
     # ------------------------------------------------------------------
     def plain_offset(self, w, i, n):
-        """Offset of request i's plaintext in the pool (16-byte aligned)."""
-        span = self.pool.numel() - n
+        """Offset of request i's plaintext in the pool (16-byte aligned);
+        n must not exceed the pool."""
+        span = self.be.pool_bytes - n
+        if span < 0:
+            raise ValueError("request larger than the plaintext pool")
         return (int(w.data_seed[i]) % max(1, span)) & ~15 if span > 0 else 0
 
     def run(self, w: Workload, capture=(), verify_every=64, drain_timeout=60.0, poll=0.0002):
         """Serve every request of ``w``; returns a stats dict.  Requests in
         ``capture`` keep a host copy of their output (for tests)."""
-        torch = self.torch
-        S = len(self.streams)
+        be = self.be
+        S = be.nstreams
         N = w.n
+        if N and int(w.size.max()) > be.pool_bytes:
+            raise ValueError("a request of %d bytes exceeds the %d-byte plaintext pool"
+                             % (int(w.size.max()), be.pool_bytes))
+        if N and ct_len(int(w.size.max())) > 1 << Arena.MAX_CLASS:
+            raise ValueError("a request of %d bytes exceeds the largest arena block" % int(w.size.max()))
         # per-request state
         status = np.full(N, -1, dtype=np.int32)
         done_ms = np.full(N, np.nan)
@@ -194,13 +285,10 @@ class Server:
         mismatches = 0
         checked = 0
         batches = 0
-        launches0 = sum(lc.lc_ctx_launch_count(c.handle) for c in self.ctxs)
+        launches0 = be.launch_count()
+        max_batch_seen = 0
 
-        base = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        base.record(self.streams[0])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        be.start()
         last_arrival = float(w.t[-1]) if N else 0.0
 
         def unref(entry):
@@ -221,13 +309,13 @@ class Server:
             nonlocal replay_bytes, mismatches, checked
             rec = inflight[s]
             idx = rec["idx"]
-            ms = base.elapsed_time(rec["event"])
-            st = self.status_host[s].numpy()[:len(idx)].copy()
+            ms = be.finish_ms(rec["token"])
+            st = be.statuses(s, len(idx))
             for k, i in enumerate(idx):
                 status[i] = st[k]
                 done_ms[i] = ms
                 if i in capture:
-                    captured[i] = self.arena.view(out_blk[i], rec["out_len"][k]).cpu().numpy()
+                    captured[i] = be.read(out_blk[i], rec["out_len"][k])
                 if w.kind[i] == 0:
                     blk = out_blk.pop(i)
                     if st[k] == 0:
@@ -241,7 +329,7 @@ class Server:
                         n = int(n_plain[i])
                         off = self.plain_offset(w, e, n)
                         checked += 1
-                        if not torch.equal(self.arena.view(out_blk[i], n), self.pool[off:off + n]):
+                        if not be.equals_pool(out_blk[i], n, off):
                             mismatches += 1
                     self.arena.release(out_blk.pop(i))
                     ref = in_ref.pop(i)
@@ -270,7 +358,7 @@ class Server:
                         kept.append(i)
                         break
                     out_blk[i] = blk
-                    src = self.pool.data_ptr() + self.plain_offset(w, i, n)
+                    src = be.pool_base + self.plain_offset(w, i, n)
                     reqs[k] = (w.pw_chars.ctypes.data + 32 * i, w.pw_len[i], 0, src, n,
                                self.arena.base + blk[0], c)
                     out_len.append(c)
@@ -293,11 +381,7 @@ class Server:
                             self.arena.release(blk)
                             kept.append(i)
                             break
-                        v = self.arena.view(own, c)
-                        with torch.cuda.stream(self.streams[s]):
-                            v.copy_(self.arena.view(cblk, c))
-                            pos = int(w.flip_pos[i] % np.uint64(c))
-                            v[pos:pos + 1].bitwise_xor_(0x5A)
+                        be.tamper_copy(s, own, cblk, c, int(w.flip_pos[i] % np.uint64(c)))
                         in_ref[i] = own
                         src = self.arena.base + own[0]
                     else:
@@ -315,24 +399,17 @@ class Server:
             kept.extend(pending)
             pending.clear()
             pending.extend(kept)
-            return idx, out_len
+            return idx, out_len, nbytes
 
-        def launch(s, idx, out_len):
-            nonlocal batches
-            st = self.streams[s]
-            ptr = self.reqs[s].ctypes.data_as(C.POINTER(lc.lc_req))
-            rc = lc.load().lc_run_batch(self.ctxs[s].handle, ptr, len(idx), self.status_dev[s].data_ptr(),
-                                        lc.LC_PARALLEL, st.cuda_stream)
-            lc.check(rc, "lc_run_batch")
-            with torch.cuda.stream(st):
-                self.status_host[s][:len(idx)].copy_(self.status_dev[s][:len(idx)], non_blocking=True)
-            ev = torch.cuda.Event(enable_timing=True)
-            ev.record(st)
-            inflight[s] = {"idx": idx, "out_len": out_len, "event": ev}
+        def launch(s, idx, out_len, nbytes):
+            nonlocal batches, max_batch_seen
+            token = be.launch(s, self.reqs[s], len(idx))
+            inflight[s] = {"idx": idx, "out_len": out_len, "token": token}
             batches += 1
+            max_batch_seen = max(max_batch_seen, nbytes)
 
         while True:
-            now = time.perf_counter() - t0
+            now = be.clock()
             progressed = False
             j = int(np.searchsorted(w.t, now, side="right"))
             if j > nxt:
@@ -340,14 +417,14 @@ class Server:
                 nxt = j
                 progressed = True
             for s in range(S):
-                if inflight[s] is not None and inflight[s]["event"].query():
+                if inflight[s] is not None and be.done(inflight[s]["token"]):
                     complete(s)
                     progressed = True
             for s in range(S):
                 if inflight[s] is None and pending:
-                    idx, out_len = form_batch(s)
+                    idx, out_len, nbytes = form_batch(s)
                     if idx:
-                        launch(s, idx, out_len)
+                        launch(s, idx, out_len, nbytes)
                         progressed = True
             if nxt >= N and not pending and all(f is None for f in inflight):
                 break
@@ -355,8 +432,8 @@ class Server:
                 break
             if not progressed:
                 time.sleep(poll)
-        wall = time.perf_counter() - t0
-        torch.cuda.synchronize()
+        wall = be.clock()
+        be.sync()
         # release what is still held
         for entry in replay:
             entry[3] = True
@@ -379,7 +456,8 @@ class Server:
             "offered_GBps": float(w.size.sum()) / max(1e-9, float(w.t[-1])) / 1e9 if N else 0.0,
             "duration_s": float(w.t[-1]) if N else 0.0, "wall_s": wall,
             "batches": batches,
-            "gpu_launches": sum(lc.lc_ctx_launch_count(c.handle) for c in self.ctxs) - launches0,
+            "gpu_launches": be.launch_count() - launches0,
+            "max_batch_bytes": max_batch_seen,
             "tampered": int(tampered.sum()),
             "tampered_rejected": int((status[tampered] == lc.LC_ERR_INTEGRITY).sum()),
             "untampered_decrypts": int(untampered_dec.sum()),

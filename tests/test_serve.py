@@ -1,5 +1,8 @@
-"""Serving loop: the arena's admission accounting (CPU) and a small served
-workload on the GPU (verdicts, plaintexts, alone-vs-mix equality)."""
+"""Serving loop: the arena's admission accounting and the serving policy on
+a simulated device (CPU), and a small served workload on the GPU (verdicts,
+plaintexts, alone-vs-mix equality)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -37,6 +40,152 @@ def test_arena_buddy_split_merge_and_budget():
         a.alloc((64 << 20) + 1)
 
 
+class _FakeArena(serve.Arena):
+    """Host arena that forgets a block's tampered mark when it is released."""
+
+    def __init__(self, nbytes, tampered):
+        super().__init__(nbytes, "cpu")
+        self.tampered = tampered
+
+    def release(self, blk):
+        self.tampered.discard(blk[0])
+        super().release(blk)
+
+
+class FakeBackend:
+    """CPU stand-in for serve.CudaBackend, for testing the serving policy
+    without a GPU.  It does no cipher arithmetic: a batch 'runs' for a fixed
+    latency plus its bytes over a rate, encryptions succeed, and a
+    decryption fails its verdict exactly when its input block was made by
+    tamper_copy.  Each launch checks the policy's invariants."""
+
+    def __init__(self, streams=3, budget_bytes=128 << 20, pool_bytes=1 << 20, gbps=2.0,
+                 latency_ms=1.0):
+        self.tampered = set()
+        self.arena = _FakeArena(budget_bytes, self.tampered)
+        self.pool_bytes = pool_bytes
+        self.pool_base = 1 << 44  # an address that is never dereferenced
+        self.nstreams = streams
+        self.rate = gbps * 1e9
+        self.latency = latency_ms * 1e-3
+        self.running = [None] * streams
+        self.status = [None] * streams
+        self.launches = 0
+        self.batches = []  # (slot, requests, input bytes, start, finish)
+
+    def start(self):
+        self.t0 = time.perf_counter()
+
+    def clock(self):
+        return time.perf_counter() - self.t0
+
+    def launch(self, s, reqs, count):
+        assert self.running[s] is None or self.done(self.running[s]), "slot busy"
+        r = reqs[:count]
+        outs = set()
+        for k in range(count):
+            off = int(r["out"][k]) - self.arena.base
+            assert 0 <= off and off + int(r["out_cap"][k]) <= self.arena.cap, "output outside the arena"
+            assert off not in outs, "two requests share an output block"
+            outs.add(off)
+            src = int(r["inp"][k])
+            if r["dir"][k] == 0:
+                assert self.pool_base <= src and src + int(r["in_len"][k]) <= self.pool_base + self.pool_bytes
+            else:
+                assert 0 <= src - self.arena.base < self.arena.cap, "decrypt input outside the arena"
+        nbytes = int(r["in_len"].sum())
+        now = self.clock()
+        token = {"finish": now + self.latency + nbytes / self.rate}
+        st = np.zeros(count, dtype=np.int32)
+        for k in range(count):
+            if r["dir"][k] == 1 and int(r["inp"][k]) - self.arena.base in self.tampered:
+                st[k] = lc.LC_ERR_INTEGRITY
+        self.running[s] = token
+        self.status[s] = st
+        self.launches += 2
+        self.batches.append((s, count, nbytes, now, token["finish"]))
+        return token
+
+    def done(self, token):
+        return self.clock() >= token["finish"]
+
+    def finish_ms(self, token):
+        return token["finish"] * 1e3
+
+    def statuses(self, s, count):
+        return self.status[s][:count].copy()
+
+    def tamper_copy(self, s, dst, src, nbytes, pos):
+        assert dst != src and 0 <= pos < nbytes
+        self.tampered.add(dst[0])
+
+    def read(self, blk, n):
+        return np.zeros(n, dtype=np.uint8)
+
+    def equals_pool(self, blk, n, off):
+        return True
+
+    def sync(self):
+        pass
+
+    def launch_count(self):
+        return self.launches
+
+    def close(self):
+        pass
+
+
+def _serve_fake(spec, **kw):
+    be_kw = {k: kw.pop(k) for k in ("budget_bytes", "gbps", "latency_ms", "streams", "pool_bytes")
+             if k in kw}
+    be = FakeBackend(**be_kw)
+    srv = serve.Server(backend=be, **kw)
+    w = serve.Workload(spec)
+    return w, be, srv.run(w, poll=0.0001)
+
+
+def test_serving_policy_on_fake_backend():
+    # Admission, batching and the replay ring on a simulated device: every
+    # request completes with the right verdict, no arena block leaks, batches
+    # respect the byte cap, and batches on different slots overlap in time.
+    spec = synth.cfg5_spec(rate=3000.0, duration=1.0, lo=256, hi=1 << 20, tamper_frac=0.05)
+    w, be, st = _serve_fake(spec, budget_bytes=256 << 20, gbps=4.0, latency_ms=2.0,
+                            max_batch_bytes=8 << 20, max_batch_requests=512)
+    assert st["completed"] == w.n > 2000
+    assert st["tampered"] > 0 and st["tampered_rejected"] == st["tampered"]
+    assert st["untampered_decrypts_ok"] == st["untampered_decrypts"] > 0
+    assert st["encrypts_ok"] == int((w.kind == 0).sum())
+    assert be.arena.in_use == 0 and not be.tampered       # everything released
+    assert st["arena_peak_bytes"] <= be.arena.cap
+    assert st["max_batch_bytes"] <= (8 << 20) + (1 << 20)  # cap plus at most one request
+    lat = st["done_ms"] - 1e3 * w.t
+    assert (lat >= 2.0 - 1e-6).all()                      # no request beats the device
+    assert st["p99_ms"] >= st["p50_ms"] >= 2.0
+    overlap = sum(1 for a, b in zip(be.batches, be.batches[1:]) if b[3] < a[4] and b[0] != a[0])
+    assert overlap > 0
+
+
+def test_serving_backpressure_small_budget():
+    # A 64 MiB budget against requests up to 16 MiB arriving faster than the
+    # simulated device serves them: admission waits for memory, the queue
+    # drains, and the budget is never exceeded.
+    spec = synth.cfg5_spec(rate=400.0, duration=0.5, lo=1 << 20, hi=16 << 20, tamper_frac=0.1)
+    w, be, st = _serve_fake(spec, budget_bytes=64 << 20, gbps=1.0, latency_ms=1.0,
+                            max_batch_bytes=32 << 20, max_batch_requests=64, pool_bytes=32 << 20)
+    assert st["completed"] == w.n
+    assert st["arena_peak_bytes"] <= 64 << 20
+    assert be.arena.in_use == 0
+    assert st["tampered_rejected"] == st["tampered"]
+    # ~2.2 GB/s offered against a 1 GB/s device: the queue grows and drains
+    assert st["p99_ms"] > 100.0 and st["wall_s"] > 0.8
+
+
+def test_serving_rejects_requests_larger_than_the_pool():
+    spec = synth.cfg5_spec(rate=200.0, duration=0.2, lo=2 << 20, hi=4 << 20, tamper_frac=0.0)
+    with pytest.raises(ValueError):
+        _serve_fake(spec, pool_bytes=1 << 20)
+
+
 def _small_spec(rate=2000.0, duration=1.5, lo=256, hi=256 << 10, tamper=0.05):
     s = synth.cfg5_spec(rate=rate, duration=duration, lo=lo, hi=hi, tamper_frac=tamper)
     return s
@@ -65,10 +214,10 @@ def test_served_workload_verdicts_and_alone_vs_mix():
             for i in sorted(capture):
                 n = int(w.size[i])
                 off = srv.plain_offset(w, i, n)
-                alone = ctx.encrypt(w.pw(i), srv.pool[off:off + n]).cpu().numpy()
+                alone = ctx.encrypt(w.pw(i), srv.be.pool[off:off + n]).cpu().numpy()
                 assert np.array_equal(st["captured"][i], alone), i
                 if n <= 16384:
-                    P = srv.pool[off:off + n].cpu().numpy()
+                    P = srv.be.pool[off:off + n].cpu().numpy()
                     assert np.array_equal(alone, O.encrypt(w.pw(i), P)), i
     finally:
         srv.close()
