@@ -316,13 +316,14 @@ def reference_arm(args):
 # our arm
 # ---------------------------------------------------------------------------
 
-def run_serving(seconds, rate, device, capacity_gbps):
+def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_batch_mib=256):
     """The served configuration (Poisson arrivals, log-uniform 256 B - 16 MiB,
     50/50, 2 % tampered decrypts, 48 GiB admission budget) for `seconds` of
     arrivals, then a supplementary run at 0.8x the measured batched
     capacity, labelled as such."""
     from paper_1201_3114_gb300 import serve, synth
-    srv = serve.Server(device, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30)
+    srv = serve.Server(device, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
+                       max_batch_bytes=max_batch_mib << 20, policy=policy)
     out = {}
     try:
         for label, r in (("offered", rate), ("at_0.8x_capacity", None)):
@@ -334,8 +335,9 @@ def run_serving(seconds, rate, device, capacity_gbps):
             keep = ("requests", "completed", "p50_ms", "p99_ms", "mean_ms", "served_GBps",
                     "offered_GBps", "duration_s", "wall_s", "batches", "gpu_launches", "tampered",
                     "tampered_rejected", "untampered_decrypts", "untampered_decrypts_ok",
-                    "encrypts_ok", "plaintext_checked", "plaintext_mismatches")
+                    "encrypts_ok", "plaintext_checked", "plaintext_mismatches", "max_batch_bytes")
             rec = {k: st[k] for k in keep}
+            rec["policy"] = policy
             rec["rate_req_per_s"] = r
             rec["served_over_per_message"] = None
             out[label] = rec
@@ -494,6 +496,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the served-workload run (0 = skip); 60 is the full config")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-policy", default="small_first", choices=["small_first", "fifo"],
+                    help="order in which waiting requests fill a batch")
+    ap.add_argument("--serve-batch-mib", type=int, default=256, help="bytes per served batch (cap)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="MIB",
                     help="only time one MIB-MiB parallel-mode encryption per step (a small "
                          "case for ncu captures); prints a short JSON line")
@@ -721,7 +726,8 @@ def main():
     if rank == 0 and args.serve_seconds > 0:
         del Parena, Carena, Oarena
         torch.cuda.empty_cache()
-        served = run_serving(args.serve_seconds, args.serve_rate, local, value / ws)
+        served = run_serving(args.serve_seconds, args.serve_rate, local, value / ws,
+                             args.serve_policy, args.serve_batch_mib)
 
     # ---- CPU oracle baseline
     cpu = None

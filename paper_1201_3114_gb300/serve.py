@@ -19,6 +19,7 @@ runs in the library's kernels.
 """
 import collections
 import ctypes as C
+import heapq
 import math
 import time
 
@@ -36,6 +37,14 @@ T = 8
 
 def ct_len(n):
     return n + T * max(1, -(-n // B))
+
+
+NCLASS = 24  # size classes: [0, 256), [256, 512), ... by powers of two
+
+
+def size_class(n):
+    """Power-of-two size class of an n-byte message (0 for n <= 256)."""
+    return min(NCLASS - 1, max(0, (max(1, int(n)) - 1).bit_length() - 8))
 
 
 class Arena:
@@ -232,7 +241,10 @@ class Server:
 
     def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
                  max_batch_bytes=256 << 20, max_batch_requests=8192, replay_cap_bytes=None,
-                 seed=0x5E4E, backend=None):
+                 seed=0x5E4E, backend=None, policy="small_first"):
+        if policy not in ("fifo", "small_first"):
+            raise ValueError("policy must be 'fifo' or 'small_first'")
+        self.policy = policy
         self.be = backend if backend is not None else CudaBackend(
             device, streams, budget_bytes, pool_bytes, max_batch_requests, seed)
         self.arena = self.be.arena
@@ -273,13 +285,31 @@ class Server:
         out_blk = {}                     # request -> arena block of its output
         captured = {}
         capture = set(int(c) for c in capture)
-        # Ciphertexts of completed encryptions, newest last: [enc, block, users, evicted].
-        # Decryptions replay the newest one (untampered ones share it read-only;
-        # a tampered one flips a byte in its own copy); the oldest are evicted
-        # above the replay cap and freed when their last user completes.
+        # Ciphertexts of completed encryptions, oldest first:
+        # [enc, block, users, evicted, size class].  A decryption replays the
+        # newest one of its own size class (else of the nearest class that has
+        # one): untampered ones share it read-only, a tampered one flips a
+        # byte in its own copy.  The oldest are evicted above the replay cap
+        # and freed when their last user completes.
         replay = collections.deque()
+        replay_cls = [collections.deque() for _ in range(NCLASS)]
         replay_bytes = 0
-        pending = collections.deque()
+        # Requests waiting for a slot, as a heap on (key, request): arrival
+        # order ("fifo"), or arrival order within size classes with the
+        # smallest class first ("small_first").
+        small_first = self.policy == "small_first"
+        req_cls = np.array([size_class(n) for n in w.size], dtype=np.int64)
+        pending = []
+
+        def push(i):
+            heapq.heappush(pending, ((int(req_cls[i]) if small_first else 0), i))
+
+        def pick_replay(k):
+            for d in range(NCLASS):
+                for c in ((k + d, k - d) if d else (k,)):
+                    if 0 <= c < NCLASS and replay_cls[c]:
+                        return replay_cls[c][-1]
+            return None
         inflight = [None] * S
         nxt = 0
         mismatches = 0
@@ -300,6 +330,8 @@ class Server:
             nonlocal replay_bytes
             while replay_bytes > self.replay_cap and len(replay) > 1:
                 entry = replay.popleft()
+                oldest = replay_cls[entry[4]].popleft()
+                assert oldest is entry
                 replay_bytes -= 1 << entry[1][1]
                 entry[3] = True
                 if entry[2] == 0:
@@ -319,7 +351,9 @@ class Server:
                 if w.kind[i] == 0:
                     blk = out_blk.pop(i)
                     if st[k] == 0:
-                        replay.append([i, blk, 0, False])
+                        entry = [i, blk, 0, False, int(req_cls[i])]
+                        replay.append(entry)
+                        replay_cls[entry[4]].append(entry)
                         replay_bytes += 1 << blk[1]
                     else:
                         self.arena.release(blk)
@@ -344,11 +378,9 @@ class Server:
             reqs = self.reqs[s]
             idx, out_len = [], []
             nbytes = 0
-            scan = len(pending)
-            kept = collections.deque()
-            while pending and scan > 0 and len(idx) < self.max_batch_requests and nbytes < self.max_batch_bytes:
-                scan -= 1
-                i = pending.popleft()
+            kept = []
+            while pending and len(idx) < self.max_batch_requests and nbytes < self.max_batch_bytes:
+                i = heapq.heappop(pending)[1]
                 k = len(idx)
                 if w.kind[i] == 0:
                     n = int(w.size[i])
@@ -364,10 +396,10 @@ class Server:
                     out_len.append(c)
                     nbytes += n
                 else:
-                    if not replay:
+                    entry = pick_replay(int(req_cls[i]))
+                    if entry is None:
                         kept.append(i)
                         continue
-                    entry = replay[-1]
                     e, cblk = entry[0], entry[1]
                     n = int(w.size[e])
                     c = ct_len(n)
@@ -396,9 +428,8 @@ class Server:
                     out_len.append(n)
                     nbytes += n
                 idx.append(i)
-            kept.extend(pending)
-            pending.clear()
-            pending.extend(kept)
+            for i in kept:
+                push(i)
             return idx, out_len, nbytes
 
         def launch(s, idx, out_len, nbytes):
@@ -413,7 +444,8 @@ class Server:
             progressed = False
             j = int(np.searchsorted(w.t, now, side="right"))
             if j > nxt:
-                pending.extend(range(nxt, j))
+                for i in range(nxt, j):
+                    push(i)
                 nxt = j
                 progressed = True
             for s in range(S):
@@ -440,6 +472,8 @@ class Server:
             if entry[2] == 0:
                 self.arena.release(entry[1])
         replay.clear()
+        for q in replay_cls:
+            q.clear()
 
         ok = ~np.isnan(done_ms)
         lat_ms = done_ms[ok] - 1e3 * w.t[ok]
