@@ -99,8 +99,11 @@ struct lc_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t ev_node_a = nullptr, ev_node_b = nullptr;
+    cudaGraphNode_t kernel_node = nullptr;  // the cipher kernel
+    cudaKernelNodeParams kparams{};         // its launch parameters as captured
     bool valid = false;
-    int grid = 0;
+    int grid = 0;      // CTAs of the full persistent grid
+    int cur_grid = 0;  // CTAs the executable graph launches now
   } graphs[kNumVariants];
 
   lc_launch launch{256, 0, 0, 0, 0};
@@ -230,6 +233,7 @@ void release_graph(lc_ctx* ctx) {
     g.exec = nullptr;
     g.graph = nullptr;
     g.ev_node_a = g.ev_node_b = nullptr;
+    g.kernel_node = nullptr;
     g.valid = false;
   }
 }
@@ -314,6 +318,7 @@ lc_status build_graph(lc_ctx* ctx, int v) {
   LC_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
   LC_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+  G.kernel_node = nullptr;
   for (auto nd : nodes) {
     cudaGraphNodeType ty;
     LC_CUDA(cudaGraphNodeGetType(nd, &ty));
@@ -322,9 +327,18 @@ lc_status build_graph(lc_ctx* ctx, int v) {
       LC_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
       if (ev == ep.a) G.ev_node_a = nd;
       if (ev == ep.b) G.ev_node_b = nd;
+    } else if (ty == cudaGraphNodeTypeKernel) {
+      cudaKernelNodeParams kp{};
+      LC_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+      if (kp.func == batch_kernel_ptr(v)) {
+        G.kernel_node = nd;
+        G.kparams = kp;
+      }
     }
   }
+  if (!G.kernel_node) return LC_ERR_CUDA;
   LC_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
+  G.cur_grid = G.grid;
   G.valid = true;
   return LC_OK;
 }
@@ -467,7 +481,14 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   hdr.nrows = (uint32_t)nrows;
   hdr.nmsgs = (uint32_t)count;
   hdr.status_out = status_dev;
-  hdr.rows_per_warp = rows_per_warp(nrows, (uint64_t)G.grid * (ctx->launch.threads_per_cta / 32));
+  // Grid of this launch: whole CTAs per SM, as few as give every row a
+  // thread in the first pass (the per-SM load stays the same), so that a
+  // batch smaller than the GPU leaves CTA slots for other streams' batches.
+  const uint64_t threads = ctx->launch.threads_per_cta;
+  const int full_per_sm = std::max(1, G.grid / std::max(1, ctx->sm_count));
+  const uint64_t need = (nrows + (uint64_t)ctx->sm_count * threads - 1) / ((uint64_t)ctx->sm_count * threads);
+  const int grid = ctx->sm_count * (int)std::min<uint64_t>(std::max<uint64_t>(need, 1), (uint64_t)full_per_sm);
+  hdr.rows_per_warp = rows_per_warp(nrows, (uint64_t)grid * (threads / 32));
   uint8_t* w = sg.host;
   memcpy(w, &hdr, sizeof hdr);
   w += sizeof hdr;
@@ -497,6 +518,12 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
       st = drain_timing(ctx);
       if (st != LC_OK) return st;
     }
+  }
+  if (grid != G.cur_grid) {
+    cudaKernelNodeParams kp = G.kparams;
+    kp.gridDim = dim3((unsigned)grid, 1, 1);
+    LC_CUDA(cudaGraphExecKernelNodeSetParams(G.exec, G.kernel_node, &kp));
+    G.cur_grid = grid;
   }
   LC_CUDA(cudaGraphLaunch(G.exec, s));
   ctx->launches += 2;  // cipher kernel + finalize kernel
