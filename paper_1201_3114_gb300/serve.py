@@ -241,7 +241,8 @@ class Server:
 
     def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
                  max_batch_bytes=256 << 20, max_batch_requests=8192, replay_cap_bytes=None,
-                 seed=0x5E4E, backend=None, policy="small_first"):
+                 seed=0x5E4E, backend=None, policy="small_first", max_adaptive_bytes=None,
+                 backlog_batches=4):
         if policy not in ("fifo", "small_first"):
             raise ValueError("policy must be 'fifo' or 'small_first'")
         self.policy = policy
@@ -249,6 +250,14 @@ class Server:
             device, streams, budget_bytes, pool_bytes, max_batch_requests, seed)
         self.arena = self.be.arena
         self.max_batch_bytes = max_batch_bytes
+        # Under a backlog (more than backlog_batches caps per slot waiting) a batch
+        # may grow to a 1/slots share of the waiting bytes, up to this many
+        # bytes (default 4x max_batch_bytes; 0 = off).  Bigger batches lose
+        # less to their last partial wave, so the backlog drains instead of
+        # settling into a slower regime.
+        self.max_adaptive_bytes = (4 * max_batch_bytes if max_adaptive_bytes is None
+                                   else max_adaptive_bytes)
+        self.backlog_batches = backlog_batches
         self.max_batch_requests = max_batch_requests
         self.replay_cap = replay_cap_bytes if replay_cap_bytes is not None else self.arena.cap // 4
         self.reqs = [np.zeros(max_batch_requests, dtype=REQ_DTYPE) for _ in range(self.be.nstreams)]
@@ -300,9 +309,12 @@ class Server:
         small_first = self.policy == "small_first"
         req_cls = np.array([size_class(n) for n in w.size], dtype=np.int64)
         pending = []
+        waiting_bytes = 0
 
         def push(i):
+            nonlocal waiting_bytes
             heapq.heappush(pending, ((int(req_cls[i]) if small_first else 0), i))
+            waiting_bytes += int(w.size[i])
 
         def pick_replay(k):
             for d in range(NCLASS):
@@ -375,12 +387,17 @@ class Server:
             inflight[s] = None
 
         def form_batch(s):
+            nonlocal waiting_bytes
             reqs = self.reqs[s]
             idx, out_len = [], []
             nbytes = 0
             kept = []
-            while pending and len(idx) < self.max_batch_requests and nbytes < self.max_batch_bytes:
+            cap = self.max_batch_bytes
+            if self.max_adaptive_bytes > cap and waiting_bytes > self.backlog_batches * S * cap:
+                cap = min(self.max_adaptive_bytes, max(cap, waiting_bytes // S))
+            while pending and len(idx) < self.max_batch_requests and nbytes < cap:
                 i = heapq.heappop(pending)[1]
+                waiting_bytes -= int(w.size[i])
                 k = len(idx)
                 if w.kind[i] == 0:
                     n = int(w.size[i])

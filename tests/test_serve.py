@@ -164,7 +164,7 @@ def test_serving_policy_on_fake_backend():
     assert st["encrypts_ok"] == int((w.kind == 0).sum())
     assert be.arena.in_use == 0 and not be.tampered       # everything released
     assert st["arena_peak_bytes"] <= be.arena.cap
-    assert st["max_batch_bytes"] <= (8 << 20) + (1 << 20)  # cap plus at most one request
+    assert st["max_batch_bytes"] <= 4 * (8 << 20) + (1 << 20)  # adaptive cap plus one request
     lat = st["done_ms"] - 1e3 * w.t
     assert (lat >= 2.0 - 1e-6).all()                      # no request beats the device
     assert st["p99_ms"] >= st["p50_ms"] >= 2.0
@@ -198,7 +198,7 @@ def test_small_first_policy_on_fake_backend():
     for policy in ("fifo", "small_first"):
         w, be, st = _serve_fake(spec, budget_bytes=512 << 20, gbps=0.9, latency_ms=2.0,
                                 max_batch_bytes=8 << 20, max_batch_requests=1024,
-                                pool_bytes=8 << 20, policy=policy)
+                                pool_bytes=8 << 20, policy=policy, max_adaptive_bytes=0)
         assert st["completed"] == w.n and be.arena.in_use == 0
         assert st["tampered_rejected"] == st["tampered"] > 0
         assert st["untampered_decrypts_ok"] == st["untampered_decrypts"]
@@ -208,6 +208,20 @@ def test_small_first_policy_on_fake_backend():
         assert same.mean() > 0.9
         res[policy] = st
     assert res["small_first"]["p50_ms"] < 0.6 * res["fifo"]["p50_ms"]
+
+
+def test_adaptive_cap_grows_batches_only_under_a_backlog():
+    spec = synth.cfg5_spec(rate=2500.0, duration=0.6, lo=256, hi=4 << 20, tamper_frac=0.05)
+    # over capacity: a backlog builds and batches grow past the 8 MiB cap
+    w, be, st = _serve_fake(spec, budget_bytes=512 << 20, gbps=0.8, latency_ms=2.0,
+                            max_batch_bytes=8 << 20, pool_bytes=8 << 20)
+    assert st["completed"] == w.n and be.arena.in_use == 0
+    assert (8 << 20) + (4 << 20) < st["max_batch_bytes"] <= (32 << 20) + (4 << 20)
+    # well under capacity: no backlog, batches stay at the cap
+    w, be, st = _serve_fake(spec, budget_bytes=512 << 20, gbps=20.0, latency_ms=2.0,
+                            max_batch_bytes=8 << 20, pool_bytes=8 << 20)
+    assert st["completed"] == w.n
+    assert st["max_batch_bytes"] <= (8 << 20) + (4 << 20)
 
 
 def test_serving_rejects_requests_larger_than_the_pool():
