@@ -70,3 +70,25 @@ def test_argument_errors_are_status_codes():
         assert lc.lc_ctx_set_launch(h, 48) == lc.LC_ERR_ARG
         with pytest.raises(lc.LcError):
             lc.check(lc.lc_encrypt(h, b"", P, 100, Cb, 108), "lc_encrypt")
+        # the pipelined host-buffer calls
+        import ctypes as C
+        lib = lc.load()
+        hin = np.zeros(100, dtype=np.uint8)
+        hout = np.zeros(108, dtype=np.uint8)
+        st = np.full(1, -1, dtype=np.int32)
+        b = lc.Batch([(b"pw", lc.LC_ENCRYPT, hin, 100, hout, 108)])
+        assert lib.lc_submit_batch_host(h, b.reqs, 1, st.ctypes.data, 0, None, None) == lc.LC_ERR_ARG
+        t = C.c_uint64(0)
+        assert lib.lc_submit_batch_host(h, None, 1, st.ctypes.data, 0, None, C.byref(t)) == lc.LC_ERR_ARG
+        assert lib.lc_submit_batch_host(h, b.reqs, 1, None, 0, None, C.byref(t)) == lc.LC_ERR_ARG
+        assert lib.lc_submit_batch_host(h, b.reqs, 1, st.ctypes.data, 9, None, C.byref(t)) == lc.LC_ERR_ARG
+        assert lc.lc_wait_batch_host(h, 0) == lc.LC_ERR_ARG
+        rc, t1 = lc.lc_submit_batch_host(h, b, st)
+        assert rc == lc.LC_OK and t1 > 0
+        assert lc.lc_wait_batch_host(h, t1 + 1) == lc.LC_ERR_ARG
+        assert lc.lc_wait_batch_host(h, t1) == lc.LC_OK and st[0] == lc.LC_OK
+        # a request error is a status, not a call error
+        bad = lc.Batch([(b"", lc.LC_ENCRYPT, hin, 100, hout, 108)])
+        rc, t2 = lc.lc_submit_batch_host(h, bad, st)
+        assert rc == lc.LC_OK and lc.lc_wait_batch_host(h, t2) == lc.LC_OK
+        assert st[0] == lc.LC_ERR_PASSWORD
