@@ -719,6 +719,22 @@ def main():
                        "step k's results are read)",
                "sync_value": ws * msg_bytes * args.steps / t_sync / 1e9,
                "sync_call": "lc_run_batch_host (one synchronous call per step)"}
+        # the host path's outputs equal the device path's byte for byte
+        # (a sample of messages; outside the timed region)
+        rng = np.random.default_rng(11)
+        pick = sorted(set(int(x) for x in rng.integers(0, count, 64)) | {0, count - 1})
+        b_off, a = [], 0
+        for it in items:
+            b_off.append(a)
+            a += it[5]
+        last = prev[1]
+        for m in pick:
+            n_out = items[m][5]
+            got = houts[last][b_off[m]:b_off[m] + n_out]
+            want = Oarena[o_off[m]:o_off[m] + n_out].cpu()
+            if not torch.equal(got, want):
+                raise RuntimeError("host-buffer output of message %d differs from the device path" % m)
+        e2e["outputs_checked"] = len(pick)
         del hin, houts, hbatches
 
     # ---- served workload (continuous batching), rank 0
