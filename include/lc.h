@@ -84,6 +84,15 @@ typedef struct lc_ctx lc_ctx;
 /* LC_PARAMS_VERSION of the arithmetic this library implements. */
 uint32_t lc_version(void);
 
+/* How this library was built: LC_BUILD_CHECKED is set in the checked build
+ * (compiled with -DLC_CHECKED), whose kernels validate every part-table
+ * index and part range before use, skip and record any invalid entry, and
+ * whose batch calls then wait for the batch and return LC_ERR_CUDA with the
+ * entry named in lc_last_cuda_error().  A debugging aid standing in for a
+ * memory checker; the paper has no counterpart. */
+#define LC_BUILD_CHECKED 1u
+uint32_t lc_build_flags(void);
+
 /* Static English text for a status code (never NULL). */
 const char* lc_status_string(lc_status s);
 

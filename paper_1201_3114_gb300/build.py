@@ -46,22 +46,32 @@ def _deps():
     return out
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB_PATH):
+CHECKED_DIR = os.path.join(BUILD_DIR, "checked")
+CHECKED_LIB_PATH = os.path.join(BUILD_DIR, "liblorenzcipher_checked.so")
+
+
+def _stale(lib) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if anything changed) and return the path of the library."""
-    if not force and not _stale():
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile (if anything changed) and return the path of the library.
+    checked=True builds the checked variant (-DLC_CHECKED: kernels validate
+    every part-table entry before use) into its own file."""
+    lib = CHECKED_LIB_PATH if checked else LIB_PATH
+    obj_dir = CHECKED_DIR if checked else BUILD_DIR
+    if checked:
+        extra_flags = list(extra_flags) + ["-DLC_CHECKED"]
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, src + ".o")
+        obj = os.path.join(obj_dir, src + ".o")
         cmd = [cc] + NVCC_FLAGS + list(extra_flags) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd += ["-x", "c++"]
@@ -76,13 +86,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -527,6 +527,20 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   }
   LC_CUDA(cudaGraphLaunch(G.exec, s));
   ctx->launches += 2;  // cipher kernel + finalize kernel
+#ifdef LC_CHECKED
+  {
+    // Checked build: wait for the batch and report a table index or part
+    // range the kernel found invalid (it skipped them).
+    uint32_t chk[2] = {0, 0};
+    LC_CUDA(cudaMemcpyAsync(chk, ctx->scratch_dev + 1, sizeof chk, cudaMemcpyDeviceToHost, s));
+    LC_CUDA(cudaStreamSynchronize(s));
+    if (chk[0]) {
+      snprintf(g_last_error, sizeof g_last_error, "checked build: invalid part table entry %u (flags %u)",
+               chk[1] ? chk[1] - 1u : 0u, chk[0]);
+      return LC_ERR_CUDA;
+    }
+  }
+#endif
   if (!ctx->last_batch_done)
     LC_CUDA(cudaEventCreateWithFlags(&ctx->last_batch_done, cudaEventDisableTiming));
   LC_CUDA(cudaEventRecord(ctx->last_batch_done, s));
@@ -555,6 +569,14 @@ size_t parts_of(const lc_params& p, size_t n, lc_mode m) { return nblocks_of(p, 
 extern "C" {
 
 uint32_t lc_version(void) { return LC_PARAMS_VERSION; }
+
+uint32_t lc_build_flags(void) {
+#ifdef LC_CHECKED
+  return LC_BUILD_CHECKED;
+#else
+  return 0u;
+#endif
+}
 
 const char* lc_last_cuda_error(void) { return g_last_error; }
 

@@ -408,8 +408,29 @@ __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_
       continue;              // static row past the end: go to the dynamic grab
     }
     const DevRow row = rows[r];
+#ifdef LC_CHECKED
+    // Checked build: every table index and part range is validated before
+    // use; a bad one is recorded (scratch[1] flag, scratch[2] = row + 1)
+    // and skipped instead of being dereferenced.
+    if (row.msg >= nmsgs) {
+      atomicOr(scratch + 1, 1u);
+      atomicCAS(scratch + 2, 0u, r + 1u);
+      continue;
+    }
+#endif
     DevMsg M;
     load_msg(M, msgs + row.msg);
+#ifdef LC_CHECKED
+    {
+      const bool seq = (M.flags & kFlagSequential) != 0;
+      const bool in_range = seq ? (row.b == 0) : ((uint64_t)row.b * p.block_len < M.n || (M.n == 0 && row.b == 0));
+      if (!in_range || (M.n && (!M.in || !M.out))) {
+        atomicOr(scratch + 1, 2u);
+        atomicCAS(scratch + 2, 0u, r + 1u);
+        continue;
+      }
+    }
+#endif
     const bool ok = run_row<Path>(M, row.b, p, s_theta);
     if (M.flags & kFlagDecrypt) {
       // Segmented vote: threads of the warp holding parts of the same
@@ -441,6 +462,9 @@ __global__ void finalize_kernel(const uint8_t* __restrict__ ws, const uint32_t* 
     }
     if (i < nrows) {
       const DevRow row = rows[i];
+#ifdef LC_CHECKED
+      if (row.msg >= nmsgs) continue;  // recorded by the cipher kernel
+#endif
       if (fail[row.msg]) {
         const DevMsg& M = msgs[row.msg];
         const bool seq = (M.flags & kFlagSequential) != 0;

@@ -137,6 +137,7 @@ _SIGNATURES = {
                                C.c_void_p]),
     "lc_run_batch_host": (C.c_int, [C.c_void_p, C.POINTER(lc_req), C.c_size_t, C.c_void_p,
                                     C.c_int, C.c_void_p]),
+    "lc_build_flags": (C.c_uint32, []),
     "lc_submit_batch_host": (C.c_int, [C.c_void_p, C.POINTER(lc_req), C.c_size_t, C.c_void_p,
                                        C.c_int, C.c_void_p, C.POINTER(C.c_uint64)]),
     "lc_wait_batch_host": (C.c_int, [C.c_void_p, C.c_uint64]),
@@ -254,6 +255,13 @@ def check(status, what="liblorenzcipher"):
 
 def lc_version() -> int:
     return load().lc_version()
+
+
+LC_BUILD_CHECKED = 1
+
+
+def lc_build_flags() -> int:
+    return load().lc_build_flags()
 
 
 def lc_status_string(status: int) -> str:
