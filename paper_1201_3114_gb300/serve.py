@@ -154,21 +154,25 @@ class CudaBackend:
     def nstreams(self):
         return len(self.streams)
 
-    def warmup(self, nbytes=32 << 20):
+    def warmup(self, nbytes=32 << 20, seconds=1.0, busy_bytes=256 << 20):
         """Run one batch per stream before serving, so that graph capture and
-        workspace growth do not land on the first requests."""
+        workspace growth do not land on the first requests; then keep every
+        stream busy with full-size batches for `seconds`, so that serving
+        starts on a GPU that has been under load."""
         torch = self.torch
-        n = min(nbytes, self.pool_bytes)
-        out = self.arena.alloc(ct_len(n))
-        try:
-            for s, c in enumerate(self.ctxs):
-                with torch.cuda.stream(self.streams[s]):
+        for k, n in enumerate((min(nbytes, self.pool_bytes), min(busy_bytes, self.pool_bytes))):
+            outs = [torch.empty(ct_len(n), dtype=torch.uint8, device=self.device) for _ in self.ctxs]
+            t0 = time.perf_counter()
+            while True:
+                for s, c in enumerate(self.ctxs):
                     lc.check(lc.lc_encrypt(c.handle, b"warm-up-password", self.pool_base, n,
-                                           self.arena.base + out[0], ct_len(n), lc.LC_PARALLEL,
+                                           outs[s].data_ptr(), ct_len(n), lc.LC_PARALLEL,
                                            self.streams[s]), "warm-up")
                 torch.cuda.synchronize()
-        finally:
-            self.arena.release(out)
+                if k == 0 or time.perf_counter() - t0 >= seconds:
+                    break
+            del outs
+        torch.cuda.empty_cache()
 
     def close(self):
         for c in self.ctxs:
@@ -311,10 +315,24 @@ class Server:
         pending = []
         waiting_bytes = 0
 
+        # per-request fields as Python lists (indexing numpy arrays one
+        # element at a time would dominate the loop's host time)
+        size_l, kind_l, tamper_l = w.size.tolist(), w.kind.tolist(), w.tamper.tolist()
+        flip_l, seed_l, pwlen_l = w.flip_pos.tolist(), w.data_seed.tolist(), w.pw_len.tolist()
+        cls_l = req_cls.tolist()
+        pw_base = w.pw_chars.ctypes.data
+        arena = self.arena
+        arena_base = arena.base
+        pool_base, pool_bytes = be.pool_base, be.pool_bytes
+
+        def plain_off(i, n):
+            span = pool_bytes - n
+            return (seed_l[i] % span) & ~15 if span > 0 else 0
+
         def push(i):
             nonlocal waiting_bytes
-            heapq.heappush(pending, ((int(req_cls[i]) if small_first else 0), i))
-            waiting_bytes += int(w.size[i])
+            heapq.heappush(pending, (cls_l[i] if small_first else 0, i))
+            waiting_bytes += size_l[i]
 
         def pick_replay(k):
             for d in range(NCLASS):
@@ -331,6 +349,7 @@ class Server:
         max_batch_seen = 0
 
         be.start()
+        cpu0 = time.process_time()
         last_arrival = float(w.t[-1]) if N else 0.0
 
         def unref(entry):
@@ -354,97 +373,97 @@ class Server:
             rec = inflight[s]
             idx = rec["idx"]
             ms = be.finish_ms(rec["token"])
-            st = be.statuses(s, len(idx))
+            st_a = be.statuses(s, len(idx))
+            status[idx] = st_a
+            done_ms[idx] = ms
+            st = st_a.tolist()
             for k, i in enumerate(idx):
-                status[i] = st[k]
-                done_ms[i] = ms
                 if i in capture:
                     captured[i] = be.read(out_blk[i], rec["out_len"][k])
-                if w.kind[i] == 0:
+                if kind_l[i] == 0:
                     blk = out_blk.pop(i)
                     if st[k] == 0:
-                        entry = [i, blk, 0, False, int(req_cls[i])]
+                        entry = [i, blk, 0, False, cls_l[i]]
                         replay.append(entry)
                         replay_cls[entry[4]].append(entry)
                         replay_bytes += 1 << blk[1]
                     else:
-                        self.arena.release(blk)
+                        arena.release(blk)
                 else:
                     e = src_enc[i]
                     if st[k] == 0 and (i // 2) % verify_every == 0:
                         n = int(n_plain[i])
-                        off = self.plain_offset(w, e, n)
+                        off = plain_off(e, n)
                         checked += 1
                         if not be.equals_pool(out_blk[i], n, off):
                             mismatches += 1
-                    self.arena.release(out_blk.pop(i))
+                    arena.release(out_blk.pop(i))
                     ref = in_ref.pop(i)
                     if isinstance(ref, list):
                         unref(ref)
                     else:
-                        self.arena.release(ref)
+                        arena.release(ref)
             evict()
             inflight[s] = None
 
         def form_batch(s):
             nonlocal waiting_bytes
-            reqs = self.reqs[s]
-            idx, out_len = [], []
+            idx, out_len, rows = [], [], []
             nbytes = 0
             kept = []
             cap = self.max_batch_bytes
             if self.max_adaptive_bytes > cap and waiting_bytes > self.backlog_batches * S * cap:
                 cap = min(self.max_adaptive_bytes, max(cap, waiting_bytes // S))
-            while pending and len(idx) < self.max_batch_requests and nbytes < cap:
+            limit = self.max_batch_requests
+            while pending and len(idx) < limit and nbytes < cap:
                 i = heapq.heappop(pending)[1]
-                waiting_bytes -= int(w.size[i])
-                k = len(idx)
-                if w.kind[i] == 0:
-                    n = int(w.size[i])
-                    c = ct_len(n)
-                    blk = self.arena.alloc(c)
+                waiting_bytes -= size_l[i]
+                if kind_l[i] == 0:
+                    n = size_l[i]
+                    c = n + T * (((n + B - 1) // B) or 1)
+                    blk = arena.alloc(c)
                     if blk is None:
                         kept.append(i)
                         break
                     out_blk[i] = blk
-                    src = be.pool_base + self.plain_offset(w, i, n)
-                    reqs[k] = (w.pw_chars.ctypes.data + 32 * i, w.pw_len[i], 0, src, n,
-                               self.arena.base + blk[0], c)
+                    rows.append((pw_base + 32 * i, pwlen_l[i], 0, pool_base + plain_off(i, n), n,
+                                 arena_base + blk[0], c))
                     out_len.append(c)
                     nbytes += n
                 else:
-                    entry = pick_replay(int(req_cls[i]))
+                    entry = pick_replay(cls_l[i])
                     if entry is None:
                         kept.append(i)
                         continue
                     e, cblk = entry[0], entry[1]
-                    n = int(w.size[e])
-                    c = ct_len(n)
-                    blk = self.arena.alloc(n)
+                    n = size_l[e]
+                    c = n + T * (((n + B - 1) // B) or 1)
+                    blk = arena.alloc(n)
                     if blk is None:
                         kept.append(i)
                         break
-                    if w.tamper[i]:
-                        own = self.arena.alloc(c)
+                    if tamper_l[i]:
+                        own = arena.alloc(c)
                         if own is None:
-                            self.arena.release(blk)
+                            arena.release(blk)
                             kept.append(i)
                             break
-                        be.tamper_copy(s, own, cblk, c, int(w.flip_pos[i] % np.uint64(c)))
+                        be.tamper_copy(s, own, cblk, c, flip_l[i] % c)
                         in_ref[i] = own
-                        src = self.arena.base + own[0]
+                        src = arena_base + own[0]
                     else:
                         entry[2] += 1
                         in_ref[i] = entry
-                        src = self.arena.base + cblk[0]
+                        src = arena_base + cblk[0]
                     out_blk[i] = blk
                     src_enc[i] = e
                     n_plain[i] = n
-                    reqs[k] = (w.pw_chars.ctypes.data + 32 * e, w.pw_len[e], 1, src, c,
-                               self.arena.base + blk[0], n)
+                    rows.append((pw_base + 32 * e, pwlen_l[e], 1, src, c, arena_base + blk[0], n))
                     out_len.append(n)
                     nbytes += n
                 idx.append(i)
+            if rows:
+                self.reqs[s][:len(rows)] = rows
             for i in kept:
                 push(i)
             return idx, out_len, nbytes
@@ -482,6 +501,7 @@ class Server:
             if not progressed:
                 time.sleep(poll)
         wall = be.clock()
+        host_cpu = time.process_time() - cpu0
         be.sync()
         # release what is still held
         for entry in replay:
@@ -508,6 +528,7 @@ class Server:
             "duration_s": float(w.t[-1]) if N else 0.0, "wall_s": wall,
             "batches": batches,
             "gpu_launches": be.launch_count() - launches0,
+            "host_cpu_s": host_cpu,
             "max_batch_bytes": max_batch_seen,
             "tampered": int(tampered.sum()),
             "tampered_rejected": int((status[tampered] == lc.LC_ERR_INTEGRITY).sum()),
