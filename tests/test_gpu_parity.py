@@ -677,3 +677,33 @@ def test_one_context_two_streams(ctx):
         assert (host(st) == 0).all(), k
         for y, w in zip(outs, want):
             assert np.array_equal(host(y)[:w.size], w), k
+
+
+def test_message_over_4gib_sampled(ctx):
+    # One message just over 2^32 bytes: part offsets b * 4096 and tag offsets
+    # n + 8 b pass 2^32.  Sampled parts on both sides of the boundary and the
+    # ragged last one equal the oracle; the whole message round-trips.
+    n = (1 << 32) + 3 * B + 5
+    seed = 0x4_0000_0001
+    pw = b"over-four-gibibytes"
+    P = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lc.check(lc.lc_synth_uniform(P, n, seed, 0))
+    Cd = ctx.encrypt(pw, P)
+    nb = -(-n // B)
+    assert Cd.numel() == n + T * nb
+    key = O.key_schedule(pw)
+    Ph = np.zeros(n, dtype=np.uint8)          # only the sampled parts are filled
+    Cb = np.zeros(n + T * nb, dtype=np.uint8)
+    edge = (1 << 32) // B
+    for b in (0, edge - 1, edge, edge + 1, nb - 1):
+        lo, hi = b * B, min(n, (b + 1) * B)
+        Ph[lo:hi] = synth.uniform_bytes(seed, hi - lo, lo)
+        O.encrypt_blocks(key, Ph, n, Cb, b, b + 1)
+        assert np.array_equal(host(Cd[lo:hi]), Cb[lo:hi]), b
+        assert np.array_equal(host(Cd[n + T * b:n + T * b + T]), Cb[n + T * b:n + T * b + T]), b
+    del Ph, Cb
+    st, back = ctx.decrypt(pw, Cd)
+    assert st == lc.LC_OK
+    step = 1 << 30
+    for a in range(0, n, step):
+        assert torch.equal(back[a:a + step], P[a:a + step]), a
