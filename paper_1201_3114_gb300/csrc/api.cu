@@ -1109,9 +1109,14 @@ lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t
   LC_CUDA(cudaMemcpyAsync(acc, ctx->stats_dev, sizeof acc, cudaMemcpyDeviceToHost, s));
   LC_CUDA(cudaStreamSynchronize(s));
   out->n = n;
-  for (int b = 0; b < 256; b++) out->hist[b] = acc[b];
-  out->sum = acc[256];
-  out->sum_sq = acc[257];
+  // the sums follow exactly from the histogram: sum b * count, sum b^2 * count
+  out->sum = 0;
+  out->sum_sq = 0;
+  for (int b = 0; b < 256; b++) {
+    out->hist[b] = acc[b];
+    out->sum += (uint64_t)b * acc[b];
+    out->sum_sq += (uint64_t)b * (uint64_t)b * acc[b];
+  }
   for (int k = 0; k < LC_STATS_MAX_LAG; k++) out->lag_sum[k] = (uint32_t)k < max_lag ? acc[258 + k] : 0;
   ctx->launches += 1;
   return LC_OK;

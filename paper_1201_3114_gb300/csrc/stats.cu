@@ -11,6 +11,8 @@
 // the next 8 bytes for the lagged products), form the sums of products four
 // bytes at a time with the unsigned 4-way byte dot product (__dp4a), and add
 // their partial sums to the global 64-bit totals once per CTA at the end.
+// The sum and the sum of squares are not accumulated here: they follow
+// exactly from the histogram (the host forms them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,7 +36,7 @@ __device__ __forceinline__ uint32_t guarded_word(const uint8_t* data, uint64_t i
   return v;
 }
 
-// acc layout (uint64): [0, 256) histogram, 256 sum, 257 sum of squares,
+// acc layout (uint64): [0, 256) histogram, 256 and 257 unused (zero),
 // 258 + k - 1 for lag k = 1..max_lag: sum of x_i x_{i+k}.
 //
 // `data` here is 16-byte aligned; the caller's unaligned head is counted by
@@ -48,7 +50,6 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
   uint32_t* const hl = hist + lane;
-  uint64_t s1 = 0, s2 = 0;
   uint64_t lag[LC_STATS_MAX_LAG];
 #pragma unroll
   for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] = 0;
@@ -59,8 +60,6 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
     for (uint32_t i = 0; i < h; i++) {
       const uint32_t x = head[i];
       atomicAdd(&hl[x * 32u], 1u);
-      s1 += x;
-      s2 += x * x;
       if (kLags) {
         for (uint32_t k = 1; k <= LC_STATS_MAX_LAG; k++) {
           const uint64_t j = (uint64_t)i + k;  // position in head + data
@@ -77,7 +76,6 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
     const uint64_t end = base + kTile < m ? base + kTile : m;
     // 32-bit partial sums per tile: a thread adds 8 chunks of 32 bytes per
     // tile, so every partial stays below 256 * 255^2 < 2^32.
-    uint32_t t1 = 0, t2 = 0;
     uint32_t tl[LC_STATS_MAX_LAG];
 #pragma unroll
     for (int k = 0; k < LC_STATS_MAX_LAG; k++) tl[k] = 0;
@@ -104,11 +102,6 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
         for (int j = 0; j < 8; j++) w[j] = guarded_word(data, i + 4 * j, m);
         for (uint32_t q = 0; q < kChunk && i + q < m; q++)
           atomicAdd(&hl[((w[q >> 2] >> (8 * (q & 3))) & 255u) << 5], 1u);
-      }
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        t1 = __dp4a(w[j], 0x01010101u, t1);
-        t2 = __dp4a(w[j], w[j], t2);
       }
       if (kLags) {
         if (i + kChunk + 8 <= m) {
@@ -140,8 +133,6 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
         }
       }
     }
-    s1 += t1;
-    s2 += t2;
 #pragma unroll
     for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k];
   }
@@ -153,19 +144,13 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
     for (uint32_t c = 0; c < 32; c++) t += hist[b * 32u + ((c + b) & 31u)];
     if (t) atomicAdd(acc + b, (unsigned long long)t);
   }
-  // warp-reduce the scalar sums, then one atomic per warp
-  for (int off = 16; off; off >>= 1) {
-    s1 += __shfl_down_sync(0xFFFFFFFFu, s1, off);
-    s2 += __shfl_down_sync(0xFFFFFFFFu, s2, off);
-    if (kLags) {
+  // warp-reduce the lagged sums, then one atomic per warp and lag
+  if (kLags) {
+    for (int off = 16; off; off >>= 1) {
 #pragma unroll
       for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += __shfl_down_sync(0xFFFFFFFFu, lag[k], off);
     }
-  }
-  if (lane == 0) {
-    atomicAdd(acc + 256, (unsigned long long)s1);
-    atomicAdd(acc + 257, (unsigned long long)s2);
-    if (kLags) {
+    if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < LC_STATS_MAX_LAG; k++)
         if (k < (int)max_lag) atomicAdd(acc + 258 + k, (unsigned long long)lag[k]);
