@@ -229,8 +229,33 @@ class CudaBackend:
         return self.arena.view(blk, n).cpu().numpy()
 
     def equals_pool(self, blk, n, off):
-        """Whether n bytes of an arena block equal the pool at off (on the device)."""
+        """Whether n bytes of an arena block equal the pool at off (synchronous)."""
         return bool(self.torch.equal(self.arena.view(blk, n), self.pool[off:off + n]))
+
+    def verify_async(self, s, blk, n, off):
+        """Compare n bytes of an arena block with the pool at off on slot s's
+        stream, counting a mismatch on the device; nothing waits.  The block
+        must not be reused before fence(s)'s token is done."""
+        torch = self.torch
+        if not hasattr(self, "mismatch_dev"):
+            self.mismatch_dev = torch.zeros(self.nstreams, dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(self.streams[s]):
+            diff = torch.ne(self.arena.view(blk, n), self.pool[off:off + n]).any()
+            self.mismatch_dev[s:s + 1].add_(diff.to(torch.int32).reshape(1))
+
+    def fence(self, s):
+        """A token that is done once the work enqueued on slot s so far is."""
+        ev = self.torch.cuda.Event()
+        ev.record(self.streams[s])
+        return ev
+
+    def mismatches(self):
+        """Mismatches counted by verify_async (waits for the device)."""
+        if not hasattr(self, "mismatch_dev"):
+            return 0
+        n = int(self.mismatch_dev.sum().item())
+        self.mismatch_dev.zero_()
+        return n
 
     def sync(self):
         self.torch.cuda.synchronize()
@@ -306,6 +331,7 @@ class Server:
         # and freed when their last user completes.
         replay = collections.deque()
         replay_cls = [collections.deque() for _ in range(NCLASS)]
+        fenced = collections.deque()  # (token, blocks) released once the token is done
         replay_bytes = 0
         # Requests waiting for a slot, as a heap on (key, request): arrival
         # order ("fifo"), or arrival order within size classes with the
@@ -373,6 +399,7 @@ class Server:
             rec = inflight[s]
             idx = rec["idx"]
             ms = be.finish_ms(rec["token"])
+            held = []
             st_a = be.statuses(s, len(idx))
             status[idx] = st_a
             done_ms[idx] = ms
@@ -392,19 +419,28 @@ class Server:
                 else:
                     e = src_enc[i]
                     if st[k] == 0 and (i // 2) % verify_every == 0:
+                        # compared on the device without waiting; the block
+                        # is held until the comparison has run
                         n = int(n_plain[i])
-                        off = plain_off(e, n)
+                        be.verify_async(s, out_blk[i], n, plain_off(e, n))
                         checked += 1
-                        if not be.equals_pool(out_blk[i], n, off):
-                            mismatches += 1
-                    arena.release(out_blk.pop(i))
+                        held.append(out_blk.pop(i))
+                    else:
+                        arena.release(out_blk.pop(i))
                     ref = in_ref.pop(i)
                     if isinstance(ref, list):
                         unref(ref)
                     else:
                         arena.release(ref)
+            if held:
+                fenced.append((be.fence(s), held))
             evict()
             inflight[s] = None
+
+        def release_fenced():
+            while fenced and be.done(fenced[0][0]):
+                for blk in fenced.popleft()[1]:
+                    arena.release(blk)
 
         def form_batch(s):
             nonlocal waiting_bytes
@@ -488,6 +524,7 @@ class Server:
                 if inflight[s] is not None and be.done(inflight[s]["token"]):
                     complete(s)
                     progressed = True
+            release_fenced()
             for s in range(S):
                 if inflight[s] is None and pending:
                     idx, out_len, nbytes = form_batch(s)
@@ -503,7 +540,13 @@ class Server:
         wall = be.clock()
         host_cpu = time.process_time() - cpu0
         be.sync()
+        mismatches += be.mismatches()
         # release what is still held
+        release_fenced()
+        for _, blks in fenced:
+            for blk in blks:
+                arena.release(blk)
+        fenced.clear()
         for entry in replay:
             entry[3] = True
             if entry[2] == 0:

@@ -70,6 +70,7 @@ class FakeBackend:
         self.rate = gbps * 1e9
         self.latency = latency_ms * 1e-3
         self.running = [None] * streams
+        self.verified = 0
         self.device_free = 0.0
         self.status = [None] * streams
         self.launches = 0
@@ -131,6 +132,18 @@ class FakeBackend:
 
     def equals_pool(self, blk, n, off):
         return True
+
+    def verify_async(self, s, blk, n, off):
+        assert 0 <= blk[0] and blk[0] + n <= self.arena.cap and 0 <= off and off + n <= self.pool_bytes
+        self.verified += 1
+
+    def fence(self, s):
+        # done once slot s's latest batch has finished
+        run = self.running[s]
+        return {"finish": run["finish"] if run is not None else 0.0}
+
+    def mismatches(self):
+        return 0
 
     def sync(self):
         pass
