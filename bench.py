@@ -24,6 +24,7 @@ Multi-GPU (torchrun, N > 1): every rank runs its own copy of the workload
 (weak scaling, no data-path collective); timing is max over ranks.
 """
 import argparse
+import collections
 import hashlib
 import json
 import math
@@ -668,55 +669,62 @@ def main():
         hin_tot = sum(it[3] for it in items)
         hout_tot = sum(it[5] for it in items)
         hin = torch.empty(hin_tot, dtype=torch.uint8).pin_memory()
-        # two sets of outputs and statuses: a step's results stay intact while
-        # the next step's copies run
-        houts = [torch.empty(hout_tot, dtype=torch.uint8).pin_memory() for _ in range(2)]
-        hitems = [[], []]
+        # one set of outputs and statuses per batch the library keeps in
+        # flight: a step's results stay intact while later steps' copies run
+        NS = lc.LC_HOST_INFLIGHT
+        houts = [torch.empty(hout_tot, dtype=torch.uint8).pin_memory() for _ in range(NS)]
+        hitems = [[] for _ in range(NS)]
         a, b_ = 0, 0
         for m, it in enumerate(items):
             src = Parena if it[1] == 0 else Carena
             off = (p_off[m] if it[1] == 0 else c_off[m])
             hin[a:a + it[3]].copy_(src[off:off + it[3]])
-            for j in range(2):
+            for j in range(NS):
                 hitems[j].append((it[0], it[1], hin.data_ptr() + a, it[3], houts[j].data_ptr() + b_, it[5]))
             a += it[3]
             b_ += it[5]
-        hbatches = [lc.Batch(hitems[j]) for j in range(2)]
-        hstats = [np.zeros(count, dtype=np.int32) for _ in range(2)]
-        for j in range(2):
+        hbatches = [lc.Batch(hitems[j]) for j in range(NS)]
+        hstats = [np.zeros(count, dtype=np.int32) for _ in range(NS)]
+        for j in range(NS):
             lc.check(lc.lc_run_batch_host(ctx.handle, hbatches[j], hstats[j], lc.LC_PARALLEL, stream))
             assert (hstats[j] == 0).all()
         # one synchronous call per step
         barrier()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            lc.check(lc.lc_run_batch_host(ctx.handle, hbatches[k % 2], hstats[k % 2], lc.LC_PARALLEL,
+            lc.check(lc.lc_run_batch_host(ctx.handle, hbatches[k % NS], hstats[k % NS], lc.LC_PARALLEL,
                                           stream))
-            if not (hstats[k % 2] == 0).all():
+            if not (hstats[k % NS] == 0).all():
                 raise RuntimeError("host-buffer batch failed")
         t_sync = max_over_ranks(time.perf_counter() - t0, dev if ws > 1 else None)
-        # pipelined: step k+1 is submitted before step k's results are read,
-        # so its input copies overlap step k's kernel
+        # pipelined: up to NS - 1 steps are submitted ahead of the one whose
+        # results are read, so uploads, kernels and downloads of neighbouring
+        # steps overlap
         barrier()
         t0 = time.perf_counter()
-        prev = None
+        queue = collections.deque()
+
+        def retire():
+            t_old, j_old = queue.popleft()
+            lc.check(lc.lc_wait_batch_host(ctx.handle, t_old), "lc_wait_batch_host")
+            if not (hstats[j_old] == 0).all():
+                raise RuntimeError("host-buffer batch failed")
+            return j_old
+
+        last = None
         for k in range(args.steps):
-            rc, t = lc.lc_submit_batch_host(ctx.handle, hbatches[k % 2], hstats[k % 2], lc.LC_PARALLEL,
+            rc, t = lc.lc_submit_batch_host(ctx.handle, hbatches[k % NS], hstats[k % NS], lc.LC_PARALLEL,
                                             stream)
             lc.check(rc, "lc_submit_batch_host")
-            if prev is not None:
-                lc.check(lc.lc_wait_batch_host(ctx.handle, prev[0]), "lc_wait_batch_host")
-                if not (hstats[prev[1]] == 0).all():
-                    raise RuntimeError("host-buffer batch failed")
-            prev = (t, k % 2)
-        lc.check(lc.lc_wait_batch_host(ctx.handle, prev[0]), "lc_wait_batch_host")
-        if not (hstats[prev[1]] == 0).all():
-            raise RuntimeError("host-buffer batch failed")
+            queue.append((t, k % NS))
+            if len(queue) >= NS:
+                last = retire()
+        while queue:
+            last = retire()
         t_e2e = max_over_ranks(time.perf_counter() - t0, dev if ws > 1 else None)
         e2e = {"value": ws * msg_bytes * args.steps / t_e2e / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": hin_tot, "d2h_bytes_per_step": hout_tot + 4 * count,
-               "call": "lc_submit_batch_host + lc_wait_batch_host (step k+1 submitted before "
-                       "step k's results are read)",
+               "call": "lc_submit_batch_host + lc_wait_batch_host (%d steps in flight)" % NS,
                "sync_value": ws * msg_bytes * args.steps / t_sync / 1e9,
                "sync_call": "lc_run_batch_host (one synchronous call per step)"}
         # the host path's outputs equal the device path's byte for byte
@@ -727,7 +735,6 @@ def main():
         for it in items:
             b_off.append(a)
             a += it[5]
-        last = prev[1]
         for m in pick:
             n_out = items[m][5]
             got = houts[last][b_off[m]:b_off[m] + n_out]

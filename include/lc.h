@@ -187,7 +187,7 @@ lc_status lc_run_batch_host(lc_ctx* ctx, const lc_req* reqs, size_t count,
 
 /* Host-buffer batches a context can hold in flight (one device staging area
  * each). */
-#define LC_HOST_INFLIGHT 2u
+#define LC_HOST_INFLIGHT 3u
 
 /* lc_run_batch_host without the wait, so that consecutive batches overlap:
  * batch k+1's input copies run while batch k computes, and batch k's output

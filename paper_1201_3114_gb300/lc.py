@@ -20,7 +20,7 @@ LC_OK, LC_ERR_ARG, LC_ERR_PASSWORD, LC_ERR_LENGTH, LC_ERR_INTEGRITY = 0, 1, 2, 3
 LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_NOMEM = 5, 6, 7
 LC_PARALLEL, LC_SEQUENTIAL = 0, 1
 LC_ENCRYPT, LC_DECRYPT = 0, 1
-LC_HOST_INFLIGHT = 2
+LC_HOST_INFLIGHT = 3
 
 # objects a submitted host batch reads or writes after the call returns,
 # kept alive until its ticket is waited for: {(ctx, ticket): refs}
