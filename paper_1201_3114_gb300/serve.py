@@ -290,6 +290,18 @@ class Server:
         self.max_batch_requests = max_batch_requests
         self.replay_cap = replay_cap_bytes if replay_cap_bytes is not None else self.arena.cap // 4
         self.reqs = [np.zeros(max_batch_requests, dtype=REQ_DTYPE) for _ in range(self.be.nstreams)]
+        if backend is None:
+            self.dry_run()
+
+    def dry_run(self, seconds=3.0, rate=5000.0):
+        """Serve a short synthetic workload at moderate load and discard the
+        result.  The first run of the loop in a process was measured slow for
+        its first seconds (every small device operation of the request path
+        took ~10x longer on the host), and at a load near capacity the
+        backlog it leaves does not drain; a second run in the same process
+        was not affected."""
+        spec = synth.cfg5_spec(rate=rate, duration=seconds, lo=256, hi=1 << 20, tamper_frac=0.02)
+        self.run(Workload(spec), verify_every=8)
 
     def close(self):
         self.be.close()
