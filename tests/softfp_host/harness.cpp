@@ -1,0 +1,415 @@
+// harness.cpp -- checks the integer-path binary64 routines of
+// csrc/softfp64.cuh, compiled for the host, against the host's IEEE-754
+// arithmetic: round to nearest, ties to even (IEEE 754-2019 Sec. 4.3.1) for
+// a + b, a - b, a * b, 10 a and 28 a, and floor(RN(a * 10^13)) converted to
+// int64 with saturation (low 32 bits) for the scaled floor.
+//
+// Operands come from generated classes (a full grid of exponent pairs,
+// the cipher's value range, every adder gap with tie and sticky bit
+// patterns, cancellations, constructed halfway cases ...).  For each
+// (operation, class) it prints one line
+//
+//   <op> <class> <cases> <integer-path cases> <integer-path halfway cases>
+//        <mismatches> [first mismatch]
+//
+// and exits 1 if any result differs.  NaN results compare equal to any NaN:
+// which NaN an IEEE unit returns is not fixed by the standard.
+//
+// usage: harness <scale> [threads]   (cases per class = base count * scale)
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "softfp64.cuh"
+
+namespace S = lc::sfp;
+
+namespace {
+
+enum Op { ADD, SUB, MUL, MUL10, MUL28, FLOOR13, NOPS };
+const char* const kOpName[NOPS] = {"add", "sub", "mul", "mul10", "mul28", "floor13"};
+
+constexpr uint64_t kFrac = 0x000FFFFFFFFFFFFFull;
+
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014), one stream per task
+struct Gen {
+  uint64_t s;
+  uint64_t u64() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  uint32_t below(uint32_t n) { return (uint32_t)(((u64() >> 32) * n) >> 32); }
+  int range(int lo, int hi) { return lo + (int)below((uint32_t)(hi - lo + 1)); }
+  double unit() { return (double)(u64() >> 11) * 0x1.0p-53; }
+  double sign() { return (u64() & 1u) ? -1.0 : 1.0; }
+};
+
+uint64_t to_bits(double x) {
+  uint64_t b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+}
+double of_bits(uint64_t b) {
+  double x;
+  memcpy(&x, &b, sizeof x);
+  return x;
+}
+double make(uint64_t sign, uint32_t e, uint64_t frac) {
+  return of_bits((sign & 1u) << 63 | (uint64_t)(e & 0x7FFu) << 52 | (frac & kFrac));
+}
+
+// significands with structure in their low bits as well as plain random ones
+uint64_t frac_pattern(Gen& g) {
+  switch (g.below(8)) {
+    case 0: return 0;
+    case 1: return kFrac;
+    case 2: return 1;
+    case 3: return g.u64() & kFrac & ~0xFFFFull;
+    case 4: return (g.u64() & kFrac) | 0xFFFFull;
+    default: return g.u64() & kFrac;
+  }
+}
+
+// low w bits: zero, exactly half, half plus or minus one, or random
+uint64_t low_pattern(Gen& g, uint32_t w) {
+  const uint64_t mask = (w >= 64) ? ~0ull : ((1ull << w) - 1);
+  const uint64_t half = w ? 1ull << (w - 1) : 0;
+  switch (g.below(6)) {
+    case 0: return 0;
+    case 1: return half;
+    case 2: return (half + 1) & mask;
+    case 3: return (half - 1) & mask;
+    case 4: return mask;
+    default: return g.u64() & mask;
+  }
+}
+
+double cipher_value(Gen& g) {
+  static const double kScale[4] = {1.0, 1e-2, 1e-4, 1e3};
+  return (g.unit() * 160.0 - 80.0) * kScale[g.below(4)];
+}
+double wide_value(Gen& g) { return g.sign() * ldexp(1.0 + g.unit(), g.range(-1080, 1080)); }
+double few_bits_value(Gen& g) { return g.sign() * (double)g.range(1, 4095) * ldexp(1.0, g.range(-40, 40)); }
+
+uint64_t ref_floor13(double a) {
+  const double v = a * 1e13;
+  int64_t r;
+  if (isnan(v)) r = 0;
+  else if (floor(v) >= 9223372036854775808.0) r = INT64_MAX;
+  else if (floor(v) < -9223372036854775808.0) r = INT64_MIN;
+  else r = (int64_t)floor(v);
+  return (uint32_t)(uint64_t)r;
+}
+
+uint64_t ref(Op op, double a, double b) {
+  switch (op) {
+    case ADD: return to_bits(a + b);
+    case SUB: return to_bits(a - b);
+    case MUL: return to_bits(a * b);
+    case MUL10: return to_bits(10.0 * a);
+    case MUL28: return to_bits(28.0 * a);
+    case FLOOR13: return ref_floor13(a);
+    default: return 0;
+  }
+}
+
+uint64_t soft(Op op, double a, double b) {
+  switch (op) {
+    case ADD: return S::bits(S::dadd(a, b));
+    case SUB: return S::bits(S::dsub(a, b));
+    case MUL: return S::bits(S::dmul(a, b));
+    case MUL10: return S::bits(S::mul_small<5, 1>(a));
+    case MUL28: return S::bits(S::mul_small<7, 2>(a));
+    case FLOOR13: return S::floor_scaled_lo32(a);
+    default: return 0;
+  }
+}
+
+// Whether the exact result lies halfway between two binary64 values: the
+// rounding error of r, exact by TwoSum (Knuth, TAOCP vol. 2, 4.2.2) or by a
+// fused multiply-add, is half an ulp of r (or of the binade below, when r
+// is a power of two reached by rounding up).  Used only to count the
+// halfway cases a class exercises.
+bool is_tie(Op op, double a, double b) {
+  double r, e;
+  switch (op) {
+    case ADD:
+    case SUB: {
+      const double y = op == ADD ? b : -b;
+      r = a + y;
+      const double bb = r - a;
+      e = (a - (r - bb)) + (y - bb);
+      break;
+    }
+    case MUL: r = a * b; e = fma(a, b, -r); break;
+    case MUL10: r = 10.0 * a; e = fma(10.0, a, -r); break;
+    case MUL28: r = 28.0 * a; e = fma(28.0, a, -r); break;
+    case FLOOR13: r = a * 1e13; e = fma(a, 1e13, -r); break;
+    default: return false;
+  }
+  if (!isfinite(r) || !isfinite(e) || r == 0.0 || e == 0.0 || fabs(r) < 0x1p-1020) return false;
+  const int k = ilogb(r);
+  if (fabs(e) == ldexp(1.0, k - 53)) return true;
+  return fabs(r) == ldexp(1.0, k) && fabs(e) == ldexp(1.0, k - 54) && (e < 0) != (r < 0);
+}
+
+bool same(Op op, uint64_t x, uint64_t y) {
+  if (x == y) return true;
+  return op != FLOOR13 && isnan(of_bits(x)) && isnan(of_bits(y));
+}
+
+// floor13 operands whose product with 10^13 lies exactly halfway between
+// two binary64 values: M 5^13 = q 2^s + 2^(s-1), s = 30 or 31.
+double floor_tie(Gen& g) {
+  const uint64_t five13 = 1220703125ull;
+  for (;;) {
+    const uint32_t s = 30u + (uint32_t)g.below(2);
+    // inverse of 5^13 modulo 2^64 (Newton iteration), reduced mod 2^s
+    uint64_t inv = five13;
+    for (int k = 0; k < 6; k++) inv *= 2 - five13 * inv;
+    const uint64_t mod = (1ull << s) - 1;
+    const uint64_t low = ((inv & mod) << (s - 1)) & mod;
+    const uint64_t M = (((uint64_t)g.range(1 << 21, (1 << 22) - 1) << 31) | low) & ((1ull << 53) - 1);
+    if (M < (1ull << 52)) continue;
+    const unsigned __int128 P = (unsigned __int128)M * five13;
+    int bl = 0;
+    for (unsigned __int128 t = P; t; t >>= 1) bl++;
+    if (bl != 53 + (int)s) continue;
+    return g.sign() * ldexp((double)M, g.range(-20, 6) - 52);
+  }
+}
+
+struct ClassDef {
+  const char* name;
+  uint64_t base;  // cases at scale 1
+};
+
+// Classes of each operation; gen() fills (a, b) for case i of class c.
+std::vector<ClassDef> classes(Op op) {
+  if (op == ADD || op == SUB)
+    return {{"exp_grid", 2048ull * 2048 * 2}, {"cipher", 2u << 20}, {"wide", 1u << 20},
+            {"few_bits", 1u << 20},          {"gap", 4u << 20},    {"cancel", 2u << 20},
+            {"ties", 2u << 20},              {"ties_far", 1u << 20}};
+  if (op == MUL)
+    return {{"exp_grid", 2048ull * 2048 * 2}, {"cipher", 2u << 20},      {"wide", 1u << 20},
+            {"few_bits", 2u << 20},          {"result_edge", 2u << 20}, {"cipher_consts", 2u << 20}};
+  if (op == FLOOR13)
+    return {{"exp_grid", 2048ull * 2 * 512}, {"cipher", 4u << 20}, {"wide", 1u << 20}, {"few_bits", 1u << 20},
+            {"ties", 1u << 18},               {"exact_int", 1u << 20}, {"small", 1u << 20}};
+  return {{"exp_grid", 2048ull * 2 * 512}, {"cipher", 4u << 20}, {"wide", 1u << 20}, {"few_bits", 1u << 20}};
+}
+
+void gen(Op op, const char* cls, uint64_t i, Gen& g, double* a, double* b) {
+  const bool two = op == ADD || op == SUB || op == MUL;
+  *b = 0.0;
+  if (!strcmp(cls, "exp_grid")) {
+    if (two) {
+      *a = make(g.u64(), (uint32_t)(i % 2048), frac_pattern(g));
+      *b = make(g.u64(), (uint32_t)((i / 2048) % 2048), frac_pattern(g));
+    } else {
+      *a = make((i / 2048) & 1u, (uint32_t)(i % 2048), frac_pattern(g));
+    }
+    return;
+  }
+  if (!strcmp(cls, "cipher")) {
+    *a = cipher_value(g);
+    if (two) *b = cipher_value(g);
+    return;
+  }
+  if (!strcmp(cls, "wide")) {
+    *a = wide_value(g);
+    if (two) *b = wide_value(g);
+    return;
+  }
+  if (!strcmp(cls, "few_bits")) {
+    if (two) {
+      *a = g.sign() * ldexp(1.0 + g.unit(), g.range(-60, 60));
+      *b = few_bits_value(g);
+    } else {
+      *a = few_bits_value(g);
+    }
+    return;
+  }
+  if (!strcmp(cls, "gap")) {
+    // every exponent gap 0..71 over the whole exponent range, with the bits
+    // of b that fall below a's last place set to tie and sticky patterns
+    const uint32_t ea = (uint32_t)g.range(1, 2046);
+    const uint32_t d = (uint32_t)(i % 72);
+    const uint32_t eb = ea > d ? ea - d : 0;
+    uint32_t w = d + (uint32_t)g.below(3);  // d - 1, d or d + 1
+    w = w < 1 ? 1 : (w - 1 < 52 ? w - 1 : 52);
+    const uint64_t fb = ((g.u64() & kFrac) & ~((1ull << w) - 1)) | low_pattern(g, w);
+    *a = make(g.u64(), ea, g.u64());
+    *b = make(g.u64(), eb, fb);
+    if (g.below(2)) std::swap(*a, *b);
+    return;
+  }
+  if (!strcmp(cls, "cancel")) {
+    // b = -a (add) or a (sub) with its last bits perturbed, and a (1 - 2^-k)
+    const double x = g.sign() * ldexp(1.0 + g.unit(), g.range(-1000, 1000));
+    const uint64_t pert = to_bits(x) ^ (g.u64() & 0xFFFull);
+    double y = g.below(2) ? of_bits(pert) : x * (1.0 - ldexp(1.0, -g.range(1, 60)));
+    if (op == ADD) y = -y;
+    *a = x;
+    *b = y;
+    return;
+  }
+  if (!strcmp(cls, "ties")) {
+    // gap d in [1, 31] and the bits of b below a's last place set to exactly
+    // half of the place the sum rounds at (one place up after a carry, one
+    // down after a borrow)
+    const uint32_t ea = (uint32_t)g.range(33, 2046);
+    const uint32_t d = (uint32_t)g.range(1, 31);
+    const int w = (int)d + g.range(-1, 1);
+    const uint64_t fb = (g.u64() & kFrac & ~((2ull << (w > 0 ? w : 0)) - 1)) | (w > 0 ? 1ull << (w - 1) : 0);
+    *a = make(g.u64(), ea, g.u64());
+    *b = make(g.u64(), ea - d, fb);
+    return;
+  }
+  if (!strcmp(cls, "ties_far")) {
+    // t + h with h half an ulp of t (or 3/2), at every scale
+    const int k = g.range(-1000, 1000);
+    const double t = g.sign() * ldexp((double)((1ull << 52) | (g.u64() & kFrac)), k - 52);
+    static const double kH[4] = {1.0, 3.0, -1.0, -3.0};
+    const double h = ldexp(1.0, k - 53) * kH[g.below(4)];
+    *a = t;
+    *b = (op == SUB) ? -h : h;
+    return;
+  }
+  if (!strcmp(cls, "result_edge")) {
+    // products whose exponent lands next to the normal range's ends
+    const uint32_t ea = (uint32_t)g.range(1, 2046);
+    const int target = g.below(2) ? g.range(-3, 6) : g.range(2040, 2050);
+    int eb = target - (int)ea + 1023;
+    eb = eb < 0 ? 0 : (eb > 2047 ? 2047 : eb);
+    *a = make(g.u64(), ea, frac_pattern(g));
+    *b = make(g.u64(), (uint32_t)eb, frac_pattern(g));
+    return;
+  }
+  if (!strcmp(cls, "cipher_consts")) {
+    static const double kC[8] = {0.01, 8.0 / 3.0, 10.0, 28.0, 1e13, 1.0, 0.5, 3.0};
+    *a = cipher_value(g);
+    *b = kC[g.below(8)];
+    return;
+  }
+  if (!strcmp(cls, "exact_int")) {
+    // k / 10^13: products at or next to an integer
+    *a = (double)((int64_t)(g.u64() % (1ull << 46)) - (int64_t)(1ull << 45)) / 1e13;
+    return;
+  }
+  if (!strcmp(cls, "small")) {
+    *a = ldexp(g.unit() * 2.0 - 1.0, g.range(-60, 40));
+    return;
+  }
+  *a = 0.0;
+}
+
+struct Result {
+  uint64_t cases = 0, fast = 0, ties = 0, bad = 0;
+  double a = 0, b = 0;
+  uint64_t sw = 0, want = 0;
+};
+
+// floor13's "ties" class is built by rejection sampling; it is generated
+// here rather than in gen() to keep gen() cheap for the other classes.
+void run_task(Op op, const char* cls, uint64_t lo, uint64_t hi, uint64_t seed, Result* r) {
+  Gen g{seed};
+  const bool floor_ties = op == FLOOR13 && !strcmp(cls, "ties");
+  for (uint64_t i = lo; i < hi; i++) {
+    double a, b = 0.0;
+    if (floor_ties) a = floor_tie(g);
+    else gen(op, cls, i, g, &a, &b);
+    sfp_host::hw_calls = 0;
+    const uint64_t s = soft(op, a, b);
+    const bool fast = sfp_host::hw_calls == 0;
+    const uint64_t w = ref(op, a, b);
+    r->cases++;
+    r->fast += fast;
+    if (fast && is_tie(op, a, b)) r->ties++;
+    if (!same(op, s, w)) {
+      if (!r->bad) {
+        r->a = a;
+        r->b = b;
+        r->sw = s;
+        r->want = w;
+      }
+      r->bad++;
+    }
+  }
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  const double scale = argc > 1 ? atof(argv[1]) : 1.0;
+  unsigned nthreads = argc > 2 ? (unsigned)atoi(argv[2]) : std::thread::hardware_concurrency();
+  if (nthreads < 1) nthreads = 1;
+
+  struct Task {
+    Op op;
+    size_t cls;
+    uint64_t lo, hi;
+  };
+  std::vector<Task> tasks;
+  std::vector<std::vector<ClassDef>> defs(NOPS);
+  std::vector<std::vector<Result>> res(NOPS);
+  for (int o = 0; o < NOPS; o++) {
+    defs[o] = classes((Op)o);
+    res[o].resize(defs[o].size());
+    for (size_t c = 0; c < defs[o].size(); c++) {
+      const uint64_t n = (uint64_t)((double)defs[o][c].base * scale);
+      const uint64_t chunk = 1u << 18;
+      for (uint64_t lo = 0; lo < n; lo += chunk) tasks.push_back({(Op)o, c, lo, std::min(n, lo + chunk)});
+    }
+  }
+  std::atomic<size_t> next{0};
+  std::mutex mu;
+  auto worker = [&]() {
+    for (;;) {
+      const size_t t = next.fetch_add(1);
+      if (t >= tasks.size()) return;
+      const Task& T = tasks[t];
+      Result r;
+      const uint64_t seed = 0x5EEDull * 1000003u + (uint64_t)T.op * 7919u + T.cls * 104729u + T.lo;
+      run_task(T.op, defs[T.op][T.cls].name, T.lo, T.hi, seed, &r);
+      std::lock_guard<std::mutex> lk(mu);
+      Result& R = res[T.op][T.cls];
+      if (r.bad && !R.bad) {
+        R.a = r.a;
+        R.b = r.b;
+        R.sw = r.sw;
+        R.want = r.want;
+      }
+      R.cases += r.cases;
+      R.fast += r.fast;
+      R.ties += r.ties;
+      R.bad += r.bad;
+    }
+  };
+  std::vector<std::thread> th;
+  for (unsigned k = 0; k < nthreads; k++) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+
+  uint64_t total_bad = 0;
+  for (int o = 0; o < NOPS; o++)
+    for (size_t c = 0; c < defs[o].size(); c++) {
+      const Result& R = res[o][c];
+      printf("%s %s %llu %llu %llu %llu", kOpName[o], defs[o][c].name, (unsigned long long)R.cases,
+             (unsigned long long)R.fast, (unsigned long long)R.ties, (unsigned long long)R.bad);
+      if (R.bad)
+        printf(" a=%a b=%a soft=%016llx want=%016llx", R.a, R.b, (unsigned long long)R.sw,
+               (unsigned long long)R.want);
+      printf("\n");
+      total_bad += R.bad;
+    }
+  return total_bad ? 1 : 0;
+}
