@@ -11,6 +11,7 @@ run independent parts of a message through the oracle at once (the
 multi-core CPU baseline does this).
 """
 import ctypes as C
+import os
 import threading
 
 import numpy as np
@@ -82,11 +83,14 @@ _u8p = C.POINTER(C.c_uint8)
 
 
 def lib():
-    """Load (building first if needed) the oracle shared object."""
+    """Load (building first if needed) the oracle shared object.  The
+    environment variable LCO_LIBRARY names another build of the same source
+    to load instead (used by the test that plants mistakes in copies of the
+    oracle and requires the pins to catch them)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build_oracle()
+            path = os.environ.get("LCO_LIBRARY") or _build.build_oracle()
             L = C.CDLL(path)
             P, K, S, ST = C.POINTER(Params), C.POINTER(Key), C.POINTER(State), C.POINTER(Stats)
             sig = {

@@ -21,10 +21,17 @@
  *   lco_rbyte           hand-derived integer values (Eq. 8)
  *   lco_encode/decode   the Caesar cipher of Sec. 1, exhaustive D(E(x)) = x
  *   lco_step_byte       frozen-dynamics special cases that reduce to a Caesar
- *                       key stream (Sec. 1) plus per-sub-step relations
- *                       (Sec. 3.2, Steps 1-3)
+ *                       key stream (Sec. 1); each sub-step of Steps 1-3
+ *                       (Sec. 3.2) against closed forms of one Euler step on
+ *                       the z-axis and at (0, y, z): the kick target r[mu_3],
+ *                       Theta, kick before F, the mu / alpha / Omega order,
+ *                       r += a' last, decryption kicking with the recovered P
+ *   lco_block_begin     the start point (Eq. 5 + part offset) and the warm-up
+ *                       length as z0 (1 - beta dt)^n_warm on the z-axis
  *   lco_encrypt/decrypt round trip, tamper rejection, parallel == sequential
  *                       where the split is trivial (Sec. 2, Sec. 5)
+ * Copies of lco.c with planted misreadings (tests/test_oracle_mutants.py)
+ * must each fail one of these pins.
  * The ciphertext values of a full chaotic run are not printed in the paper:
  * for those the oracle is the definition ("parity unpinned" against printed
  * values; pinned only through the invariants above).
