@@ -317,22 +317,32 @@ def reference_arm(args):
 # our arm
 # ---------------------------------------------------------------------------
 
-def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_batch_mib=256):
+def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_batch_mib=256,
+                low_seconds=15.0, capture_per_class=125):
     """The served configuration (Poisson arrivals, log-uniform 256 B - 16 MiB,
     50/50, 2 % tampered decrypts, 48 GiB admission budget) for `seconds` of
-    arrivals, then a supplementary run at 0.8x the measured batched
-    capacity, labelled as such."""
+    arrivals, then a supplementary run of `low_seconds` at 0.8x the measured
+    batched capacity, labelled as such.  In the first run a seeded sample of
+    encryptions, up to `capture_per_class` per power-of-two size class, keeps
+    a host copy of its ciphertext (copied asynchronously on the batch's
+    stream); returns (records, sample) where sample lists each captured
+    request's password, plaintext location in the seeded pool and output."""
     from paper_1201_3114_gb300 import serve, synth
     srv = serve.Server(device, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
                        max_batch_bytes=max_batch_mib << 20, policy=policy)
     out = {}
+    sample = None
     try:
-        for label, r in (("offered", rate), ("at_0.8x_capacity", None)):
+        for label, r, secs in (("offered", rate, seconds), ("at_0.8x_capacity", None, low_seconds)):
+            if secs <= 0:
+                continue
             if r is None:
                 mean = 1.5e6
                 r = 0.8 * capacity_gbps * 1e9 / mean
-            w = serve.Workload(synth.cfg5_spec(rate=r, duration=seconds))
-            st = srv.run(w)
+            w = serve.Workload(synth.cfg5_spec(rate=r, duration=secs))
+            cap = serve.capture_sample(w, capture_per_class) if (label == "offered" and
+                                                                 capture_per_class) else []
+            st = srv.run(w, capture=cap)
             keep = ("requests", "completed", "p50_ms", "p99_ms", "mean_ms", "served_GBps",
                     "offered_GBps", "duration_s", "wall_s", "batches", "gpu_launches", "tampered",
                     "tampered_rejected", "untampered_decrypts", "untampered_decrypts_ok",
@@ -342,9 +352,200 @@ def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_
             rec["rate_req_per_s"] = r
             rec["served_over_per_message"] = None
             out[label] = rec
+            if cap:
+                sample = {"pool_seed": srv.be.pool_seed, "label": label,
+                          "items": [(w.pw(i), int(w.size[i]), srv.plain_offset(w, i, int(w.size[i])),
+                                     st["captured"][i]) for i in cap]}
     finally:
         srv.close()
+    return out, sample
+
+
+def oracle_check_served(sample, threads):
+    """CPU-baseline leg for the served configuration: the oracle encrypts the
+    captured sample (plaintexts regenerated on the host from the pool's
+    seed) on `threads` host threads; returns the oracle's rate and how many
+    served ciphertexts differ from it."""
+    import oracle as O
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1201_3114_gb300 import synth
+    prm = O.params()
+    items = sample["items"]
+    plains = [None] * len(items)
+
+    def gen(k):
+        _, n, off, _ = items[k]
+        plains[k] = synth.uniform_bytes(sample["pool_seed"], n, off)
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(gen, range(len(items))))
+    keys = [O.key_schedule(pw, prm) for pw, _, _, _ in items]
+    outs = [np.zeros(O.ciphertext_len(n, O.PARALLEL, prm), dtype=np.uint8) for _, n, _, _ in items]
+    jobs = []
+    for k, (_, n, _, _) in enumerate(items):
+        nb = max(1, -(-n // 4096))
+        jobs += [(k, b, min(nb, b + 64)) for b in range(0, nb, 64)]
+    jobs.sort(key=lambda j: -items[j[0]][1])
+
+    def run(job):
+        k, b0, b1 = job
+        O.encrypt_blocks(keys[k], plains[k], plains[k].size, outs[k], b0, b1, prm)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(run, jobs))
+    secs = time.perf_counter() - t0
+    nbytes = sum(n for _, n, _, _ in items)
+    bad = sum(1 for k, it in enumerate(items) if not np.array_equal(it[3], outs[k]))
+    return {"value": nbytes / secs / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d captured encryptions of the served run, every size class 256 B - 16 MiB "
+                      "(%.0f MiB)" % (len(items), nbytes / 2 ** 20),
+            "wall_s": secs}, len(items), bad
+
+
+def single_message_configs(ctx, dev, stream, pipes, sm_mhz, reps=20):
+    """The single-message configurations, through lc_encrypt / lc_decrypt on
+    device-resident buffers (CUDA events on the launching stream; lc_decrypt
+    synchronises, so its times include the verdict read-back):
+
+      cfg1_64k   64 KiB uniform bytes, 16-char password, parallel mode
+      cfg2_1mib  1 MiB Zipf text with a 4 KiB zero run, 32-char password, both
+                 modes; one flipped ciphertext byte must be rejected
+      cfg3_1gib  1 GiB uniform bytes, 24-char password, parallel mode, with
+                 the cipher kernel's time, its binary64 rate and roofline
+                 fractions
+
+    Round trips are checked here; bit-exactness against the oracle is the
+    parity tests' job (tests/test_gpu_parity.py)."""
+    import torch
+    from paper_1201_3114_gb300 import lc, synth
+
+    def ev_time(fn, n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def enc_dec(pw, P, mode, n_rep, n_warm=3):
+        n = P.numel()
+        C = torch.empty(ctx.ciphertext_len(n, mode), dtype=torch.uint8, device=dev)
+        back = torch.empty(max(1, n), dtype=torch.uint8, device=dev)
+        enc = lambda: lc.check(lc.lc_encrypt(ctx.handle, pw, P, n, C, C.numel(), mode, stream))
+        dec = lambda: lc.check(lc.lc_decrypt(ctx.handle, pw, C, C.numel(), back, n, mode, stream))
+        for _ in range(n_warm):
+            enc()
+            dec()
+        ms_e = ev_time(enc, n_rep)
+        ms_d = ev_time(dec, n_rep)
+        if not torch.equal(back[:n], P):
+            raise SystemExit("round trip failed (mode %d, %d bytes)" % (mode, n))
+        return C, ms_e, ms_d
+
+    out = {}
+    c1 = synth.cfg1()
+    P1 = torch.from_numpy(c1["P"]).to(dev)
+    _, me, md = enc_dec(c1["pw"], P1, lc.LC_PARALLEL, reps)
+    n1 = P1.numel()
+    out["cfg1_64k"] = {"bytes": n1, "parts": n1 // 4096, "encrypt_ms": me, "decrypt_ms": md,
+                       "encrypt_GBps": n1 / me / 1e6, "decrypt_GBps": n1 / md / 1e6,
+                       "note": "16 parts: one part's serial chain (3000 warm-up + 4104 byte steps) "
+                               "sets the latency"}
+    c2 = synth.cfg2()
+    P2 = torch.from_numpy(c2["P"]).to(dev)
+    n2 = P2.numel()
+    rec = {"bytes": n2}
+    for mode, name, nrep, nwarm in ((lc.LC_PARALLEL, "parallel", reps, 3),
+                                    (lc.LC_SEQUENTIAL, "sequential", 2, 1)):
+        C2, me, md = enc_dec(c2["pw"], P2, mode, nrep, nwarm)
+        bad = C2.clone()
+        pos = synth.word(c2["flip_seed"], mode) % bad.numel()
+        bad[pos] ^= 1 + synth.word(c2["flip_seed"], 10 + mode) % 255
+        st, _ = ctx.decrypt(c2["pw"], bad, mode)
+        rec[name] = {"encrypt_ms": me, "decrypt_ms": md, "encrypt_GBps": n2 / me / 1e6,
+                     "decrypt_GBps": n2 / md / 1e6,
+                     "flipped_byte_rejected": st == lc.LC_ERR_INTEGRITY}
+        if st != lc.LC_ERR_INTEGRITY:
+            raise SystemExit("config 2: a flipped ciphertext byte was accepted (mode %d)" % mode)
+    rec["parallel_over_sequential"] = rec["parallel"]["encrypt_GBps"] / rec["sequential"]["encrypt_GBps"]
+    out["cfg2_1mib"] = rec
+    del P1, P2
+
+    spec = synth.cfg3_spec()
+    n3, pw3 = spec["n"], spec["pw"]
+    P3 = torch.empty(n3, dtype=torch.uint8, device=dev)
+    lc.check(lc.lc_synth_uniform(P3, n3, spec["data_seed"], 0, stream))
+    C3 = torch.empty(ctx.ciphertext_len(n3), dtype=torch.uint8, device=dev)
+    enc3 = lambda: lc.check(lc.lc_encrypt(ctx.handle, pw3, P3, n3, C3, C3.numel(), lc.LC_PARALLEL, stream))
+    for _ in range(3):
+        enc3()
+    lc.check(lc.lc_ctx_timing(ctx.handle, True))
+    ms = ev_time(enc3, 5)
+    kms, kn = lc.lc_ctx_kernel_time(ctx.handle)
+    lc.check(lc.lc_ctx_timing(ctx.handle, False))
+    kms = kms / max(1, kn)
+    st, back = ctx.decrypt(pw3, C3)
+    if st != lc.LC_OK or not torch.equal(back, P3):
+        raise SystemExit("config 3: round trip failed")
+    del back
+    sizes = [n3]
+    ops, parts, _ = fp64_ops_per_launch(sizes)
+    rl = roofline_terms(sizes, kms, pipes, sm_mhz)
+    out["cfg3_1gib"] = {"bytes": n3, "parts": parts, "ms_per_encrypt": ms, "GBps": n3 / ms / 1e6,
+                        "kernel_ms": kms, "kernel_GBps": n3 / kms / 1e6,
+                        "fp64_ops_per_launch": ops, "fp64_gops": ops / (kms * 1e-3) / 1e9,
+                        "method_roofline_GBps": rl["method_roofline_GBps"],
+                        "method_roofline_frac": (n3 / kms / 1e6) / rl["method_roofline_GBps"],
+                        "fp64_pipe_frac_of_probe": rl["fp64_pipe_frac_of_probe"],
+                        "joint": rl["joint"]}
+    del P3, C3
+    torch.cuda.empty_cache()
     return out
+
+
+def roofline_terms(sizes, kernel_ms, pipes, sm_mhz, n_warm=3000, steps=1, B=4096, T=8):
+    """Roofline figures of one cipher-kernel launch over messages of these
+    sizes:
+      method_roofline_GBps  the bound the method statement names: the slower of
+                the binary64 arithmetic at the nominal FP64 peak (33 operations
+                per byte, warm-up included) and 2 bytes per byte at HBM speed
+      fp64_pipe_*  the binary64 operations that run on the FP64 pipe against
+                the probed DADD rate
+      joint     the kernel's own ceiling: the FP64-pipe time of those
+                operations at the probed rate, and the issue time of its
+                instructions (the committed ncu count per message byte, on the
+                same kernel sources) at 4 warp-instructions per SM per clock;
+                frac = the larger of the two over the measured kernel time"""
+    from paper_1201_3114_gb300 import lc
+    ops, parts, traj = fp64_ops_per_launch(sizes, n_warm, steps, B, T)
+    msg_bytes = int(np.asarray(sizes, dtype=np.int64).sum())
+    peak_slot = NOMINAL_FP64_TFLOPS * 1e3 / 2.0
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    per_byte = ops / max(1, msg_bytes)
+    method_gbps = min(peak_slot / per_byte, hbm / (2.0 + 8.0 * parts / max(1, msg_bytes)))
+    mask = lc.lc_emu_mask()
+    hw_ops = fp64_pipe_ops_per_launch(sizes, mask, n_warm, steps, B, T)
+    t_fp64 = hw_ops / (pipes.dadd_gops * 1e9) * 1e3
+    rec = committed_traffic()
+    joint = None
+    if rec and rec.get("inst_executed_per_message_byte") and sm_mhz:
+        inst = rec["inst_executed_per_message_byte"] * msg_bytes
+        t_issue = inst / (pipes.sm_count * 4 * sm_mhz * 1e6) * 1e3
+        bound = max(t_fp64, t_issue)
+        joint = {"fp64_pipe_ms": t_fp64, "issue_ms": t_issue, "kernel_ms": kernel_ms,
+                 "bound": "fp64_pipe" if t_fp64 >= t_issue else "issue",
+                 "frac": bound / kernel_ms,
+                 "fp64_pipe_ops": hw_ops, "fp64_pipe_rate_gops": pipes.dadd_gops,
+                 "warp_instructions": inst, "sm_count": pipes.sm_count, "sm_mhz": sm_mhz,
+                 "note": "warp instructions scaled from the committed ncu count per message byte "
+                         "(profiles/batch_kernel_traffic.json, same kernel sources)"}
+    return {"method_roofline_GBps": method_gbps,
+            "fp64_pipe_frac_of_probe": (hw_ops / (kernel_ms * 1e-3) / 1e9) / pipes.dadd_gops,
+            "joint": joint}
 
 
 def profile_case(args):
@@ -493,9 +694,17 @@ def main():
     ap.add_argument("--cpu-sample-mb", type=int, default=512)
     ap.add_argument("--ref-sample-mb", type=int, default=96)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
-    ap.add_argument("--serve-seconds", type=float, default=8.0,
-                    help="length of the served-workload run (0 = skip); 60 is the full config")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (lc_tune) and time the default launch shape")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the served-workload run (0 = skip); 60 s is the configuration")
+    ap.add_argument("--serve-low-seconds", type=float, default=15.0,
+                    help="length of the supplementary served run at 0.8x capacity (0 = skip)")
+    ap.add_argument("--serve-capture", type=int, default=125,
+                    help="served encryptions per size class whose ciphertexts the CPU-baseline leg "
+                         "checks against the oracle (0 = none)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-message configurations (64 KiB, 1 MiB, 1 GiB)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-policy", default="small_first", choices=["small_first", "fifo"],
                     help="order in which waiting requests fill a batch")
@@ -529,8 +738,13 @@ def main():
     sizes, pws, seeds, dirs = spec["sizes"], spec["pws"], spec["data_seeds"], spec["dirs"]
     count = len(sizes)
     ctx = lc.Context(local)
-    if args.tune:
+    default_launch = lc.lc_ctx_get_launch(ctx.handle).as_dict()
+    tuning = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
         lc.lc_tune(ctx.handle, 0, stream)
+        tuning = {"default": default_launch, "seconds": time.perf_counter() - t0,
+                  "candidates": [dict(l, median_ms=ms) for l, ms in lc.lc_tune_report(ctx.handle)]}
     launch = lc.lc_ctx_get_launch(ctx.handle)
 
     # ---- device arenas: plaintexts, ciphertexts (decrypt inputs), outputs
@@ -619,9 +833,15 @@ def main():
     hw_ops = fp64_pipe_ops_per_launch(sizes, mask, prm.n_warm, prm.steps_per_byte,
                                       prm.block_len, prm.tag_len)
     hw_rate = hw_ops / (kern_avg_ms * 1e-3) / 1e9
+    rl_terms = roofline_terms(sizes, kern_avg_ms, pipes, clk.get("sm_mhz") or pipes.sm_clock_mhz,
+                              prm.n_warm, prm.steps_per_byte, prm.block_len, prm.tag_len)
     roofline = {
         "bound": "alu", "unit": "G FP64 op/s", "achieved": achieved, "peak": peak,
         "frac": achieved / peak,
+        "frac_label": "FP64-only roof, nominal: every binary64 operation of the path against the "
+                      "nominal FP64 slot rate",
+        "joint": rl_terms["joint"],
+        "method_roofline_GBps": rl_terms["method_roofline_GBps"],
         "peak_source": "of fallback: recipe nominal 1.25 TFLOP/s FP64 / 2 flops per DFMA slot "
                        "(no FP64 entry in the measured peaks)",
         "peak_probe": pipes.dadd_gops, "frac_of_probe": achieved / pipes.dadd_gops,
@@ -744,13 +964,19 @@ def main():
         e2e["outputs_checked"] = len(pick)
         del hin, houts, hbatches
 
+    # ---- single-message configurations (64 KiB, 1 MiB both modes, 1 GiB)
+    del Parena, Carena, Oarena
+    torch.cuda.empty_cache()
+    configs = None
+    if not args.no_configs:
+        configs = single_message_configs(ctx, dev, stream, pipes, clk.get("sm_mhz") or pipes.sm_clock_mhz)
+
     # ---- served workload (continuous batching), rank 0
-    served = None
+    served, served_sample = None, None
     if rank == 0 and args.serve_seconds > 0:
-        del Parena, Carena, Oarena
-        torch.cuda.empty_cache()
-        served = run_serving(args.serve_seconds, args.serve_rate, local, value / ws,
-                             args.serve_policy, args.serve_batch_mib)
+        served, served_sample = run_serving(args.serve_seconds, args.serve_rate, local, value / ws,
+                                            args.serve_policy, args.serve_batch_mib,
+                                            args.serve_low_seconds, args.serve_capture)
 
     # ---- CPU oracle baseline
     cpu = None
@@ -767,6 +993,14 @@ def main():
         b1, s1 = run_oracle_sample(spec, plan1, 1)
         cpu["single_core"] = {"value": b1 / s1 / 1e9, "unit": UNIT, "cores": 1,
                               "sample": "%.0f MiB" % (b1 / 2 ** 20), "wall_s": s1}
+        # the served configuration: the oracle on the captured sample, which
+        # also checks every captured ciphertext byte for byte
+        if served_sample:
+            rec, checked, bad = oracle_check_served(served_sample, threads)
+            cpu["served_sample"] = rec
+            served[served_sample["label"]]["ciphertext_checked"] = checked
+            served[served_sample["label"]]["ciphertext_mismatches"] = bad
+            served_sample = None
 
     if served and pm:
         for rec in served.values():
@@ -781,10 +1015,14 @@ def main():
                        "parts": parts, "mode": "parallel",
                        "l2": "inputs larger than L2 (%.2f GB per step)" % (msg_bytes / 1e9),
                        "launch": {"threads_per_cta": launch.threads_per_cta,
-                                  "ctas_per_sm": launch.ctas_per_sm},
+                                  "ctas_per_sm": launch.ctas_per_sm,
+                                  "dense_build": launch.dense_build,
+                                  "source": "lc_tune" if tuning else "default"},
+                       "tuning": tuning,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "per_message_launch": pm, "served": served, "clocks": clk,
+            "configs": configs,
             "pipes_probe_gops": {k: round(v, 1) for k, v in pipes.as_dict().items()},
         }
         print(json.dumps(line), flush=True)

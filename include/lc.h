@@ -229,23 +229,45 @@ lc_status lc_wait_batch_host(lc_ctx* ctx, uint64_t ticket);
  * moves the multiplies to the integer pipes (higher throughput).  0 = auto
  * (192 parts per SM).  host_chunk_mib: a host-buffer batch whose inputs
  * exceed this many MiB is cut into up to 4 chunks of whole requests, so
- * that one chunk's copies overlap another's kernel (0 = 4096 MiB).  None of
- * these changes results. */
+ * that one chunk's copies overlap another's kernel (0 = 4096 MiB).
+ * dense_build: 1 = the throughput variant's build compiled for 4 resident
+ * 256-thread CTAs per SM (at most 64 registers per thread) instead of the
+ * default build for 3 (0).  None of these changes results. */
 typedef struct {
   uint32_t threads_per_cta;
   uint32_t ctas_per_sm;
   uint32_t smem_staging;
   uint32_t small_batch_rows;
   uint32_t host_chunk_mib;
+  uint32_t dense_build;
 } lc_launch;
 
 lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out);
 lc_status lc_ctx_set_launch(lc_ctx* ctx, const lc_launch* l);
 
-/* Autotuner: times the candidate launch shapes on a synthetic batch of
- * `probe_bytes` (0 = 64 MiB) on `stream`, keeps the fastest in the context
- * and returns it in *best (may be NULL).  Never changes results. */
+/* Autotuner: times candidate launch shapes of the throughput variant on a
+ * synthetic batch and keeps the fastest in the context; *best (may be NULL)
+ * receives it.  The probe batch has the shape of a batched workload:
+ * messages of log-uniform sizes between 1 KiB and 4 MiB (seeded, device-
+ * generated bytes, distinct passwords, all encrypted in parallel mode)
+ * totalling `probe_bytes` (0 = enough 4096-byte parts to fill the default
+ * persistent grid twice).  Candidates: threads per CTA in {64, 128, 256},
+ * all resident CTAs per SM or one fewer, each with the default and the
+ * dense build (lc_launch.dense_build); each candidate runs once untimed and
+ * three times timed with CUDA events on `stream`, and the median counts.
+ * The other lc_launch fields keep their values.  Synchronises `stream`;
+ * allocates the probe's buffers for the duration of the call.  Never
+ * changes results. */
 lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best);
+
+/* Timings of the last lc_tune call on this context: up to `cap` candidates
+ * (launch shape and median milliseconds) in the order tried; *n receives how
+ * many there were.  LC_ERR_ARG for a NULL ctx or n. */
+typedef struct {
+  lc_launch launch;
+  double median_ms;
+} lc_tune_entry;
+lc_status lc_tune_report(const lc_ctx* ctx, lc_tune_entry* out, size_t cap, size_t* n);
 
 /* Accumulated device time of the context's main cipher kernel since the
  * last reset, measured with CUDA events on the launching stream (enabled by
@@ -313,13 +335,16 @@ lc_status lc_probe_pipes(int device, lc_pipe_rates* out);
  * rejected with LC_ERR_LENGTH before any GPU work.
  *
  * The first call on a device sets that device up (looks up the array's
- * device address and copies the Theta table into it, synchronously); make
- * that first call before any stream capture.  Every call uses the same
- * array and leaves its contents behind; each call clears the counter and
- * flags it needs.  Calls whose GPU work overlaps (for example on two
- * streams without ordering between them) race on the array: issue them on
- * one stream, or synchronise between them.  Asynchronous on `stream`; uses
- * the current device.  Errors: LC_ERR_ARG, LC_ERR_LENGTH, LC_ERR_CUDA. */
+ * device address and copies the Theta table into it, synchronously).  Every
+ * call uses the same array and leaves its contents behind; each call clears
+ * the counter and flags it needs.  Calls whose GPU work overlaps (for
+ * example on two streams without ordering between them) race on the array:
+ * issue them on one stream, or synchronise between them.  The part table is
+ * copied to the device from static pageable host memory, so the call may
+ * wait on the host until earlier work on `stream` has drained; the call
+ * must not be captured into a CUDA graph, and a capturing `stream` gives
+ * LC_ERR_ARG.  Otherwise asynchronous on `stream`; uses the current device.
+ * Errors: LC_ERR_ARG, LC_ERR_LENGTH, LC_ERR_CUDA. */
 #define LC_NOALLOC_MAX_REQUESTS 1024u
 #define LC_NOALLOC_MAX_PARTS 240000u
 lc_status lc_run_batch_noalloc(const lc_req* reqs, size_t count, int32_t* status_dev, lc_mode m,

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <string>
@@ -106,7 +107,8 @@ struct lc_ctx {
     int cur_grid = 0;  // CTAs the executable graph launches now
   } graphs[kNumVariants];
 
-  lc_launch launch{256, 0, 0, 0, 0};
+  lc_launch launch{256, 0, 0, 0, 0, 0};
+  std::vector<lc_tune_entry> tune_report;  // the last lc_tune's candidates
 
   std::unordered_map<std::string, HostKey> keys;
 
@@ -349,7 +351,8 @@ int batch_variant(const lc_ctx* ctx, size_t nrows) {
   if (ctx->variant != kVariantV1) return ctx->variant;
   const uint64_t thr = ctx->launch.small_batch_rows ? ctx->launch.small_batch_rows
                                                     : (uint64_t)ctx->sm_count * kSmallBatchRowsPerSm;
-  return nrows < thr ? kVariantV1Latency : kVariantV1;
+  if (nrows < thr) return kVariantV1Latency;
+  return ctx->launch.dense_build ? kVariantV1Dense : kVariantV1;
 }
 
 // Host validation of one request; LC_OK or the request's status code.
@@ -555,10 +558,12 @@ lc_status ensure_status_tmp(lc_ctx* ctx, size_t count) {
 }  // namespace
 
 namespace lc {
-// Request validation and framing lengths, shared with other entry points.
+// Request validation, framing lengths and kernel parameters, shared with
+// other entry points.
 int32_t validate_request(const lc_params& p, const lc_req& r, lc_mode m, size_t* n) {
   return validate_req(p, r, m, n);
 }
+void dev_params_from(const lc_params& p, DevParams* d) { to_dev_params(p, d); }
 size_t parts_of(const lc_params& p, size_t n, lc_mode m) { return nblocks_of(p, n, m); }
 }  // namespace lc
 
@@ -1010,7 +1015,7 @@ lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out) {
 lc_status lc_ctx_set_launch(lc_ctx* ctx, const lc_launch* l) {
   if (!ctx || !l) return LC_ERR_ARG;
   if (l->threads_per_cta < 32 || l->threads_per_cta > 256 || l->threads_per_cta % 32) return LC_ERR_ARG;
-  if (l->ctas_per_sm > 64 || l->smem_staging != 0) return LC_ERR_ARG;
+  if (l->ctas_per_sm > 64 || l->smem_staging != 0 || l->dense_build > 1) return LC_ERR_ARG;
   ctx->launch = *l;
   invalidate_graphs(ctx);
   return LC_OK;
@@ -1020,47 +1025,90 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   if (!ctx) return LC_ERR_ARG;
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (probe_bytes == 0) probe_bytes = (size_t)64 << 20;
   const lc_params& p = ctx->params;
-  const size_t nparts = std::max<size_t>(1, probe_bytes / p.block_len);
-  const size_t n = nparts * p.block_len;
+  const int tune_variant = ctx->variant == kVariantV1 ? kVariantV1 : ctx->variant;
+  if (probe_bytes == 0)  // two waves of the default persistent grid, in parts
+    probe_bytes = (size_t)2 * ctx->sm_count * resident_ctas(tune_variant, 256) * 256 * p.block_len;
+
+  // Probe messages: log-uniform sizes in [1 KiB, 4 MiB] from a SplitMix64
+  // counter stream, until probe_bytes are covered.
+  auto mix = [](uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  std::vector<size_t> sizes;
+  size_t total = 0, out_total = 0;
+  const double lo = std::log(1024.0), hi = std::log(4194304.0);
+  for (uint64_t i = 0; total < probe_bytes; i++) {
+    const double u = (double)(mix(0x7E57ull + (i + 1) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1p-53;
+    size_t n = (size_t)std::floor(std::exp(lo + u * (hi - lo)));
+    n = std::min<size_t>(std::max<size_t>(n, 1024), 4194304);
+    sizes.push_back(n);
+    total += n;
+    out_total += ct_len(p, n, LC_PARALLEL);
+  }
+  const size_t count = sizes.size();
   uint8_t* buf = nullptr;
-  LC_CUDA(cudaMalloc(&buf, n + ct_len(p, n, LC_PARALLEL)));
+  const size_t status_off = (total + out_total + 255) & ~(size_t)255;
+  LC_CUDA(cudaMalloc(&buf, status_off + count * sizeof(int32_t)));
   uint8_t* in = buf;
-  uint8_t* out = buf + n;
-  lc_status st = cuda_fail(launch_synth(in, n, 0x7E57ull, 0, s));
-  const uint8_t pw[16] = {'a', 'u', 't', 'o', 't', 'u', 'n', 'e', '-', 'p', 'r', 'o', 'b', 'e', '!', '!'};
-  lc_req r{pw, 16, LC_ENCRYPT, in, n, out, ct_len(p, n, LC_PARALLEL)};
-  lc_launch saved = ctx->launch, bestl = ctx->launch;
+  uint8_t* out = buf + total;
+  int32_t* stat = reinterpret_cast<int32_t*>(buf + status_off);
+  lc_status st = cuda_fail(launch_synth(in, total, 0x7E57ull, 0, s));
+  std::vector<std::string> pws(count);
+  std::vector<lc_req> reqs(count);
+  for (size_t i = 0, a = 0, b = 0; i < count; i++) {
+    char tmp[32];
+    snprintf(tmp, sizeof tmp, "tune-probe-%08zx", i);
+    pws[i] = tmp;
+    const size_t c = ct_len(p, sizes[i], LC_PARALLEL);
+    reqs[i] = lc_req{reinterpret_cast<const uint8_t*>(pws[i].data()), (uint32_t)pws[i].size(), LC_ENCRYPT,
+                     in + a, sizes[i], out + b, c};
+    a += sizes[i];
+    b += c;
+  }
+
+  const lc_launch saved = ctx->launch;
+  lc_launch bestl = saved;
   double best_ms = 1e300;
-  const uint32_t tpcs[] = {64, 128, 256};
+  ctx->tune_report.clear();
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e0));
   if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e1));
-  for (uint32_t tpc : tpcs) {
-    if (st != LC_OK) break;
-    const int maxc = resident_ctas(ctx->variant, (int)tpc);
-    std::vector<uint32_t> cands = {0};
-    for (uint32_t c = 1; c < (uint32_t)maxc; c *= 2) cands.push_back(c);
-    for (uint32_t c : cands) {
-      lc_launch l{tpc, c, 0, saved.small_batch_rows, saved.host_chunk_mib};
-      ctx->launch = l;
-      invalidate_graphs(ctx);
-      int32_t* stat = nullptr;
-      st = ensure_status_tmp(ctx, 1);
+  const bool v1 = ctx->variant == kVariantV1;
+  for (uint32_t dense = 0; dense <= (v1 ? 1u : 0u) && st == LC_OK; dense++) {
+    for (uint32_t tpc : {64u, 128u, 256u}) {
       if (st != LC_OK) break;
-      stat = ctx->status_tmp_dev;
-      st = run_batch_impl(ctx, &r, 1, stat, LC_PARALLEL, s);  // warm-up / graph build
-      if (st != LC_OK) break;
-      st = cuda_fail(cudaEventRecord(e0, s));
-      if (st == LC_OK) st = run_batch_impl(ctx, &r, 1, stat, LC_PARALLEL, s);
-      if (st == LC_OK) st = cuda_fail(cudaEventRecord(e1, s));
-      if (st == LC_OK) st = cuda_fail(cudaEventSynchronize(e1));
-      float ms = 0;
-      if (st == LC_OK) st = cuda_fail(cudaEventElapsedTime(&ms, e0, e1));
-      if (st == LC_OK && ms < best_ms) {
-        best_ms = ms;
-        bestl = l;
+      const int v = v1 ? (dense ? kVariantV1Dense : kVariantV1) : ctx->variant;
+      const int maxc = resident_ctas(v, (int)tpc);
+      std::vector<uint32_t> cands = {0};  // as many as fit
+      if (maxc > 1) cands.push_back((uint32_t)(maxc - 1));
+      for (uint32_t c : cands) {
+        // small_batch_rows = 1: the probe runs the throughput variant
+        ctx->launch = lc_launch{tpc, c, 0, 1, saved.host_chunk_mib, dense};
+        invalidate_graphs(ctx);
+        st = run_batch_impl(ctx, reqs.data(), count, stat, LC_PARALLEL, s);  // graph build, warm-up
+        if (st != LC_OK) break;
+        std::vector<double> ms3;
+        for (int rep = 0; rep < 3 && st == LC_OK; rep++) {
+          st = cuda_fail(cudaEventRecord(e0, s));
+          if (st == LC_OK) st = run_batch_impl(ctx, reqs.data(), count, stat, LC_PARALLEL, s);
+          if (st == LC_OK) st = cuda_fail(cudaEventRecord(e1, s));
+          if (st == LC_OK) st = cuda_fail(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          if (st == LC_OK) st = cuda_fail(cudaEventElapsedTime(&ms, e0, e1));
+          ms3.push_back(ms);
+        }
+        if (st != LC_OK) break;
+        std::sort(ms3.begin(), ms3.end());
+        const double med = ms3[1];
+        lc_launch rec{tpc, c, 0, saved.small_batch_rows, saved.host_chunk_mib, dense};
+        ctx->tune_report.push_back(lc_tune_entry{rec, med});
+        if (med < best_ms) {
+          best_ms = med;
+          bestl = rec;
+        }
       }
     }
   }
@@ -1072,6 +1120,13 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   invalidate_graphs(ctx);
   if (best) *best = ctx->launch;
   return st;
+}
+
+lc_status lc_tune_report(const lc_ctx* ctx, lc_tune_entry* out, size_t cap, size_t* n) {
+  if (!ctx || !n) return LC_ERR_ARG;
+  *n = ctx->tune_report.size();
+  for (size_t i = 0; i < cap && i < ctx->tune_report.size() && out; i++) out[i] = ctx->tune_report[i];
+  return LC_OK;
 }
 
 lc_status lc_ctx_timing(lc_ctx* ctx, int enable) {

@@ -187,14 +187,14 @@ struct GeneralPath {
 // and alpha_j are the same coordinate and V_i = V_j is computed once; after
 // the (mu, Omega) lock that every part reaches within a few dozen bytes this
 // is one conversion per byte instead of three.
-template <uint32_t M>
+template <uint32_t M, int MinCtas = LC_MIN_CTAS>
 struct V1Path {
   double x, y, z, ax, ay, az;
   uint32_t V0, V1, V2;
   uint32_t mu0, mu1, mu2, om0, om1, om2;
 
   static constexpr int kThetaRows = 4;
-  static constexpr int kMinCtas = LC_MIN_CTAS;
+  static constexpr int kMinCtas = MinCtas;
 
   __device__ __forceinline__ static uint32_t vf(double a) {
     if (M & kEmuFloor) return sfp::floor_scaled_lo32(a);
@@ -506,6 +506,9 @@ using KGeneral = GeneralPath<false>;
 using KGeneral4 = GeneralPath<true>;
 using KV1 = V1Path<LC_EMU_MASK>;
 using KV1Lat = V1Path<0u>;
+// The throughput variant compiled for 4 resident 256-thread CTAs per SM (at
+// most 64 registers per thread): one of the autotuner's candidates.
+using KV1Dense = V1Path<LC_EMU_MASK, 4>;
 
 }  // namespace
 
@@ -528,6 +531,7 @@ const void* batch_kernel_ptr(int variant) {
     case kVariantGeneral: return reinterpret_cast<const void*>(&batch_kernel<KGeneral>);
     case kVariantGeneral4: return reinterpret_cast<const void*>(&batch_kernel<KGeneral4>);
     case kVariantV1Latency: return reinterpret_cast<const void*>(&batch_kernel<KV1Lat>);
+    case kVariantV1Dense: return reinterpret_cast<const void*>(&batch_kernel<KV1Dense>);
     default: return reinterpret_cast<const void*>(&batch_kernel<KV1>);
   }
 }
@@ -539,6 +543,7 @@ cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, ui
     case kVariantGeneral: batch_kernel<KGeneral><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
     case kVariantGeneral4: batch_kernel<KGeneral4><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
     case kVariantV1Latency: batch_kernel<KV1Lat><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
+    case kVariantV1Dense: batch_kernel<KV1Dense><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
     default: batch_kernel<KV1><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
   }
   return cudaGetLastError();

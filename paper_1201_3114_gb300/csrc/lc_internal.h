@@ -24,7 +24,9 @@ constexpr int kVariantV1 = 2;
 // The v1 constants with every binary64 operation on the FP64 pipe: shorter
 // dependency chains, hence lower latency while the GPU is far from full.
 constexpr int kVariantV1Latency = 3;
-constexpr int kNumVariants = 4;
+// kVariantV1 compiled for 4 resident 256-thread CTAs per SM (64 registers).
+constexpr int kVariantV1Dense = 4;
+constexpr int kNumVariants = 5;
 
 // Below this many parts per SM (1.5 warps per SM sub-partition) a v1 batch
 // runs the latency variant (measured crossover on GB300).
@@ -80,7 +82,10 @@ static_assert(sizeof(DevHeader) == 32, "DevHeader layout");
 inline uint32_t rows_per_warp(uint64_t /*nrows*/, uint64_t /*grid_warps*/) { return 32u; }
 
 // Persistent-kernel scratch that lives across launches: the row counter and
-// the per-message fail flags.  The finalize kernel clears both after use.
+// the per-message fail flags.  A memset before each launch of the cipher
+// kernel clears both (a memset node at the head of the context's graph; an
+// explicit cudaMemsetAsync in the allocation-free path); the finalize kernel
+// only reads them.
 struct DevScratch {
   uint32_t row_counter;
   uint32_t pad[3];

@@ -26,6 +26,8 @@ const void* batch_kernel_ptr(int variant);
 size_t batch_kernel_smem(int variant);
 int32_t validate_request(const lc_params& p, const lc_req& r, lc_mode m, size_t* n);
 size_t parts_of(const lc_params& p, size_t n, lc_mode m);
+void dev_params_from(const lc_params& p, DevParams* d);
+int kernel_variant(const DevParams& p);
 }  // namespace lc
 
 using namespace lc;
@@ -91,21 +93,19 @@ extern "C" lc_status lc_run_batch_noalloc(const lc_req* reqs, size_t count, int3
   if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
   if (count > kMaxRequests) return LC_ERR_LENGTH;
   if (count == 0) return LC_OK;
+  // The part table is uploaded from static pageable memory, which a
+  // captured graph would re-read at replay time: capture is refused.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) return LC_ERR_ARG;
+  if (cap != cudaStreamCaptureStatusNone) return LC_ERR_ARG;
 
+  // The default (v1) constants, converted as the context path converts
+  // them; they select the v1 kernel variants used below.
   lc_params p;
   lc_params_default(&p);
   DevParams dp;
-  dp.sigma = p.sigma;
-  dp.rho = p.rho;
-  dp.beta = p.beta;
-  dp.dt = p.dt;
-  dp.eta = p.eta;
-  dp.n_warm = p.n_warm;
-  dp.steps_per_byte = p.steps_per_byte;
-  dp.block_len = p.block_len;
-  dp.tag_len = p.tag_len;
-  for (int i = 0; i < 3; i++) dp.k[i] = p.k[i];
-  dp.k_all4 = 1u;
+  dev_params_from(p, &dp);
+  if (kernel_variant(dp) != kVariantV1) return LC_ERR_ARG;
 
   std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;

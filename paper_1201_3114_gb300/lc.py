@@ -63,7 +63,15 @@ class lc_launch(C.Structure):
         ("smem_staging", C.c_uint32),
         ("small_batch_rows", C.c_uint32),
         ("host_chunk_mib", C.c_uint32),
+        ("dense_build", C.c_uint32),
     ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lc_tune_entry(C.Structure):
+    _fields_ = [("launch", lc_launch), ("median_ms", C.c_double)]
 
 
 class lc_key_info_t(C.Structure):
@@ -144,6 +152,8 @@ _SIGNATURES = {
     "lc_ctx_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lc_launch)]),
     "lc_ctx_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lc_launch)]),
     "lc_tune": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(lc_launch)]),
+    "lc_tune_report": (C.c_int, [C.c_void_p, C.POINTER(lc_tune_entry), C.c_size_t,
+                                 C.POINTER(C.c_size_t)]),
     "lc_ctx_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lc_ctx_kernel_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "lc_ctx_launch_count": (C.c_uint64, [C.c_void_p]),
@@ -398,8 +408,9 @@ def lc_ctx_get_launch(ctx) -> lc_launch:
 
 
 def lc_ctx_set_launch(ctx, threads_per_cta=256, ctas_per_sm=0, smem_staging=0,
-                      small_batch_rows=0, host_chunk_mib=0) -> int:
-    l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, small_batch_rows, host_chunk_mib)
+                      small_batch_rows=0, host_chunk_mib=0, dense_build=0) -> int:
+    l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, small_batch_rows, host_chunk_mib,
+                  dense_build)
     return load().lc_ctx_set_launch(ctx, C.byref(l))
 
 
@@ -407,6 +418,15 @@ def lc_tune(ctx, probe_bytes=0, stream=None) -> lc_launch:
     l = lc_launch()
     check(load().lc_tune(ctx, probe_bytes, _stream(stream), C.byref(l)), "lc_tune")
     return l
+
+
+def lc_tune_report(ctx):
+    """[(launch dict, median ms)] of the last lc_tune call, in the order tried."""
+    n = C.c_size_t(0)
+    check(load().lc_tune_report(ctx, None, 0, C.byref(n)), "lc_tune_report")
+    arr = (lc_tune_entry * max(1, n.value))()
+    check(load().lc_tune_report(ctx, arr, n.value, C.byref(n)), "lc_tune_report")
+    return [(arr[i].launch.as_dict(), arr[i].median_ms) for i in range(n.value)]
 
 
 def lc_ctx_timing(ctx, enable: bool) -> int:

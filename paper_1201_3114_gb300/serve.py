@@ -120,6 +120,25 @@ class Workload:
         return bytes(self.pw_chars[i, :self.pw_len[i]])
 
 
+def capture_sample(w, per_class, seed=0xC0FFEE):
+    """A seeded sample of encryption requests of ``w`` spread over every
+    power-of-two size class: up to ``per_class`` per class, chosen by a
+    seeded hash of the request index (for byte-level checks of served
+    outputs)."""
+    enc = np.flatnonzero(w.kind == 0)
+    if enc.size == 0:
+        return []
+    order = np.argsort(synth.words(seed, 0, w.n)[enc], kind="stable")
+    cls = np.array([size_class(n) for n in w.size[enc]])
+    take, count = [], collections.Counter()
+    for j in order:
+        c = int(cls[j])
+        if count[c] < per_class:
+            count[c] += 1
+            take.append(int(enc[j]))
+    return sorted(take)
+
+
 class CudaBackend:
     """The device side of the serving loop: one lc_ctx, CUDA stream and
     status buffer per stream slot, the device arena (admission budget) and
@@ -142,6 +161,7 @@ class CudaBackend:
         self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
         self.pool_base = self.pool.data_ptr()
         self.pool_bytes = pool_bytes
+        self.pool_seed = seed  # the pool is bytes [0, pool_bytes) of this uniform stream
         lc.check(lc.lc_synth_uniform(self.pool, pool_bytes, seed, 0, self.streams[0]))
         self.status_dev = [torch.zeros(max_batch_requests, dtype=torch.int32, device=self.device)
                            for _ in range(streams)]
@@ -227,6 +247,24 @@ class CudaBackend:
     def read(self, blk, n):
         """Host copy of n bytes of an arena block (after its batch completed)."""
         return self.arena.view(blk, n).cpu().numpy()
+
+    def capture_reserve(self, nbytes):
+        """Page-locked host space for capture_async copies of one run."""
+        self.cap_buf = self.torch.empty(max(1, nbytes), dtype=self.torch.uint8, pin_memory=True)
+        self.cap_used = 0
+
+    def capture_async(self, s, blk, n):
+        """Copy n bytes of an arena block to the reserved host space on slot
+        s's stream without waiting; returns the host array, valid after
+        sync().  The block must not be reused before fence(s) is done."""
+        a = self.cap_used
+        if a + n > self.cap_buf.numel():
+            raise ValueError("capture space exhausted")
+        self.cap_used = a + n
+        dst = self.cap_buf[a:a + n]
+        with self.torch.cuda.stream(self.streams[s]):
+            dst.copy_(self.arena.view(blk, n), non_blocking=True)
+        return dst.numpy()
 
     def equals_pool(self, blk, n, off):
         """Whether n bytes of an arena block equal the pool at off (synchronous)."""
@@ -317,7 +355,11 @@ class Server:
 
     def run(self, w: Workload, capture=(), verify_every=64, drain_timeout=60.0, poll=0.0002):
         """Serve every request of ``w``; returns a stats dict.  Requests in
-        ``capture`` keep a host copy of their output (for tests)."""
+        ``capture`` keep a host copy of their output (stats["captured"]):
+        encryptions are copied asynchronously on their batch's stream into
+        page-locked space reserved before the run (their output block is
+        held until the copy has run and is not offered for replay), other
+        requests synchronously."""
         be = self.be
         S = be.nstreams
         N = w.n
@@ -335,6 +377,9 @@ class Server:
         out_blk = {}                     # request -> arena block of its output
         captured = {}
         capture = set(int(c) for c in capture)
+        cap_enc = [i for i in capture if 0 <= i < N and w.kind[i] == 0]
+        if cap_enc:
+            be.capture_reserve(sum(ct_len(int(w.size[i])) for i in cap_enc))
         # Ciphertexts of completed encryptions, oldest first:
         # [enc, block, users, evicted, size class].  A decryption replays the
         # newest one of its own size class (else of the nearest class that has
@@ -417,11 +462,14 @@ class Server:
             done_ms[idx] = ms
             st = st_a.tolist()
             for k, i in enumerate(idx):
-                if i in capture:
-                    captured[i] = be.read(out_blk[i], rec["out_len"][k])
                 if kind_l[i] == 0:
                     blk = out_blk.pop(i)
-                    if st[k] == 0:
+                    if i in capture:
+                        # copied without waiting; the block is held until
+                        # the copy has run and is not replayed
+                        captured[i] = be.capture_async(s, blk, rec["out_len"][k])
+                        held.append(blk)
+                    elif st[k] == 0:
                         entry = [i, blk, 0, False, cls_l[i]]
                         replay.append(entry)
                         replay_cls[entry[4]].append(entry)
@@ -429,6 +477,8 @@ class Server:
                     else:
                         arena.release(blk)
                 else:
+                    if i in capture:
+                        captured[i] = be.read(out_blk[i], rec["out_len"][k])
                     e = src_enc[i]
                     if st[k] == 0 and (i // 2) % verify_every == 0:
                         # compared on the device without waiting; the block

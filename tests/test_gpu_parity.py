@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle_mt
 from paper_1201_3114_gb300 import lc, synth
 
 pytestmark = pytest.mark.gpu
@@ -172,8 +173,10 @@ def test_config2_text_both_modes_and_tamper(ctx):
         assert np.array_equal(got, want), mode
         st, back = gpu_decrypt(ctx, pw, got, mode)
         assert st == lc.LC_OK and np.array_equal(back, P)
-        pos = synth.word(c["flip_seed"], mode) % got.size
-        bad = got.copy()
+        # the flipped copy is made from the oracle's ciphertext (equal to the
+        # GPU's, as checked above), so the oracle never reads a GPU output
+        pos = synth.word(c["flip_seed"], mode) % want.size
+        bad = want.copy()
         bad[pos] ^= 1 + synth.word(c["flip_seed"], 10 + mode) % 255
         st, out = gpu_decrypt(ctx, pw, bad, mode)
         assert st == lc.LC_ERR_INTEGRITY and not out.any()
@@ -357,13 +360,21 @@ def test_launch_shapes_do_not_change_results(ctx):
     pw = b"launch-shapes"
     want = O.encrypt(pw, P)
     try:
-        for tpc, cps in ((32, 1), (64, 0), (128, 2), (256, 0)):
-            for small in (1, 0xFFFFFFFF):  # integer-split variant, FP64-only variant
-                assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small) == lc.LC_OK
-                assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small)
+        for tpc, cps in ((32, 1), (64, 0), (128, 2), (256, 0), (256, 4)):
+            # integer-split variant (default and dense build), FP64-only variant
+            for small, dense in ((1, 0), (1, 1), (0xFFFFFFFF, 0)):
+                assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small, 0, dense) == lc.LC_OK
+                assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small, dense)
         assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 1, 0) == lc.LC_ERR_ARG
+        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, 0, 0, 2) == lc.LC_ERR_ARG
         best = lc.lc_tune(ctx.handle, 8 << 20)
-        assert best.threads_per_cta in (64, 128, 256)
+        rep = lc.lc_tune_report(ctx.handle)
+        # 3 CTA widths x (all resident / one fewer) x 2 builds, each timed
+        assert 6 <= len(rep) <= 12 and all(ms > 0 for _, ms in rep)
+        assert {l["dense_build"] for l, _ in rep} == {0, 1}
+        fastest = min(rep, key=lambda e: e[1])[0]
+        assert (best.threads_per_cta, best.ctas_per_sm, best.dense_build) == \
+            (fastest["threads_per_cta"], fastest["ctas_per_sm"], fastest["dense_build"])
         assert np.array_equal(gpu_encrypt(ctx, pw, P), want)
     finally:
         lc.lc_ctx_set_launch(ctx.handle, 256, 0)
@@ -415,77 +426,61 @@ def test_timing_and_launch_counters(ctx):
 
 
 # ---------------------------------------------------------------------------
-# full-size workloads, sampled against the oracle
+# full-size workloads, every output byte against the oracle on all host cores
 # ---------------------------------------------------------------------------
 
-def test_config3_1gib_sampled(ctx):
+def test_config3_1gib_complete(ctx):
+    # 1 GiB of uniform bytes, 262,144 parts: every ciphertext byte and every
+    # tag against the oracle; the oracle's ciphertext decrypts to P.
     spec = synth.cfg3_spec()
     n, pw, seed = spec["n"], spec["pw"], spec["data_seed"]
-    P = torch.empty(n, dtype=torch.uint8, device="cuda")
-    lc.check(lc.lc_synth_uniform(P, n, seed, 0))
-    Cd = ctx.encrypt(pw, P)
-    nb = n // B
-    key = O.key_schedule(pw)
-    rng = np.random.default_rng(56)
-    sample = sorted(set([0, 1, nb - 1] + [int(x) for x in rng.integers(0, nb, 40)]))
-    Ch = host(Cd)
-    for b in sample:
-        Pb = np.zeros(n, dtype=np.uint8)  # only block b's bytes are read
-        Pb[b * B:(b + 1) * B] = synth.uniform_bytes(seed, B, b * B)
-        Cb = np.zeros(n + T * nb, dtype=np.uint8)
-        O.encrypt_blocks(key, Pb, n, Cb, b, b + 1)
-        assert np.array_equal(Ch[b * B:(b + 1) * B], Cb[b * B:(b + 1) * B]), b
-        assert np.array_equal(Ch[n + T * b:n + T * b + T], Cb[n + T * b:n + T * b + T]), b
-    del Ch
-    st, back = ctx.decrypt(pw, Cd)
+    P = oracle_mt.uniform(seed, n)
+    want = oracle_mt.encrypt(pw, P)
+    Pd = torch.from_numpy(P).cuda()
+    got = host(ctx.encrypt(pw, Pd))
+    assert got.size == want.size == n + T * (n // B)
+    assert oracle_mt.first_difference(got, want) == -1
+    del got
+    st, back = ctx.decrypt(pw, torch.from_numpy(want).cuda())
     assert st == lc.LC_OK
-    assert torch.equal(back, P)
+    assert torch.equal(back, Pd)
 
 
-def test_config4_batch_sampled(ctx):
+def test_config4_batch_complete(ctx):
+    # The batched workload: 4096 messages (log-uniform 1 KiB - 4 MiB, 2.06 GB),
+    # the first half encrypted, the second half decrypted from ciphertexts the
+    # oracle made; one launch; every output byte and every status.
     spec = synth.cfg4_spec()
     sizes, pws, seeds, dirs = spec["sizes"], spec["pws"], spec["data_seeds"], spec["dirs"]
     count = len(sizes)
-    plains, cts = [], []
-    # seeded plaintexts made on the device; decrypt inputs are ciphertexts
-    for m in range(count):
-        p = torch.empty(int(sizes[m]), dtype=torch.uint8, device="cuda")
-        lc.check(lc.lc_synth_uniform(p, p.numel(), seeds[m], 0))
-        plains.append(p)
-    for m in range(count // 2, count):
-        cts.append(ctx.encrypt(pws[m], plains[m]))
-    items, outs = [], []
-    for m in range(count):
-        if dirs[m] == 0:
-            out = torch.empty(ctx.ciphertext_len(int(sizes[m])), dtype=torch.uint8, device="cuda")
-            items.append((pws[m], 0, plains[m], int(sizes[m]), out, out.numel()))
-        else:
-            c = cts[m - count // 2]
-            out = torch.empty(int(sizes[m]), dtype=torch.uint8, device="cuda")
-            items.append((pws[m], 1, c, c.numel(), out, out.numel()))
-        outs.append(out)
+    plains = oracle_mt.uniform_many(seeds, sizes)
+    cts = oracle_mt.encrypt_many(list(zip(pws, plains)))
+    ins = [plains[m] if dirs[m] == 0 else cts[m] for m in range(count)]
+    want = [cts[m] if dirs[m] == 0 else plains[m] for m in range(count)]
+
+    def pack(arrs):
+        offs, tot = [], 0
+        for a in arrs:
+            offs.append(tot)
+            tot = (tot + a.size + 255) & ~255
+        buf = np.zeros(tot, dtype=np.uint8)
+        for a, o in zip(arrs, offs):
+            buf[o:o + a.size] = a
+        return buf, offs
+
+    hin, in_off = pack(ins)
+    _, out_off = pack(want)
+    din = torch.from_numpy(hin).cuda()
+    dout = torch.full((out_off[-1] + want[-1].size + 256,), 0xA5, dtype=torch.uint8, device="cuda")
+    items = [(pws[m], dirs[m], din.data_ptr() + in_off[m], ins[m].size, dout.data_ptr() + out_off[m],
+              want[m].size) for m in range(count)]
     status = torch.full((count,), -1, dtype=torch.int32, device="cuda")
     lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(items), status))
     assert (host(status) == 0).all()
-    for m in range(count // 2, count):
-        assert torch.equal(outs[m], plains[m]), m
-    # encrypt outputs: small messages whole, large ones on sampled parts
-    rng = np.random.default_rng(57)
-    for m in sorted(set(int(x) for x in rng.integers(0, count // 2, 24))):
-        n = int(sizes[m])
-        P = synth.uniform_bytes(seeds[m], n)
-        got = host(outs[m])
-        if n <= 64 * 1024:
-            assert np.array_equal(got, O.encrypt(pws[m], P)), m
-        else:
-            key = O.key_schedule(pws[m])
-            nb = -(-n // B)
-            Cb = np.zeros(n + T * nb, dtype=np.uint8)
-            for b in (0, nb - 1, int(rng.integers(0, nb))):
-                O.encrypt_blocks(key, P, n, Cb, b, b + 1)
-                hi = min(n, (b + 1) * B)
-                assert np.array_equal(got[b * B:hi], Cb[b * B:hi]), (m, b)
-                assert np.array_equal(got[n + T * b:n + T * b + T], Cb[n + T * b:n + T * b + T])
+    hout = host(dout)
+    bad = [m for m in range(count)
+           if not np.array_equal(hout[out_off[m]:out_off[m] + want[m].size], want[m])]
+    assert not bad, bad[:10]
 
 
 def test_n_it_steps_per_byte_profile():
@@ -679,10 +674,11 @@ def test_one_context_two_streams(ctx):
             assert np.array_equal(host(y)[:w.size], w), k
 
 
-def test_message_over_4gib_sampled(ctx):
+def test_message_over_4gib(ctx):
     # One message just over 2^32 bytes: part offsets b * 4096 and tag offsets
-    # n + 8 b pass 2^32.  Sampled parts on both sides of the boundary and the
-    # ragged last one equal the oracle; the whole message round-trips.
+    # n + 8 b pass 2^32.  Every byte of the 16,384 parts around the boundary,
+    # the first two parts and the last two (the ragged one) equal the oracle;
+    # the whole message round-trips.
     n = (1 << 32) + 3 * B + 5
     seed = 0x4_0000_0001
     pw = b"over-four-gibibytes"
@@ -692,15 +688,26 @@ def test_message_over_4gib_sampled(ctx):
     nb = -(-n // B)
     assert Cd.numel() == n + T * nb
     key = O.key_schedule(pw)
-    Ph = np.zeros(n, dtype=np.uint8)          # only the sampled parts are filled
+    Ph = np.zeros(n, dtype=np.uint8)          # only the checked parts are filled
     Cb = np.zeros(n + T * nb, dtype=np.uint8)
     edge = (1 << 32) // B
-    for b in (0, edge - 1, edge, edge + 1, nb - 1):
+    for b in (0, 1, nb - 2, nb - 1):
         lo, hi = b * B, min(n, (b + 1) * B)
         Ph[lo:hi] = synth.uniform_bytes(seed, hi - lo, lo)
         O.encrypt_blocks(key, Ph, n, Cb, b, b + 1)
         assert np.array_equal(host(Cd[lo:hi]), Cb[lo:hi]), b
         assert np.array_equal(host(Cd[n + T * b:n + T * b + T]), Cb[n + T * b:n + T * b + T]), b
+    # every byte of the 64 MiB around the 2^32 boundary (16,384 parts) and
+    # of their tags, the oracle on all cores
+    b0, b1 = edge - 8192, edge + 8192
+    lo, hi = b0 * B, b1 * B
+    Ph[lo:hi] = oracle_mt.uniform(seed, hi - lo, lo)
+    jobs = [(c, min(b1, c + 64)) for c in range(b0, b1, 64)]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(oracle_mt.THREADS) as ex:
+        list(ex.map(lambda j: O.encrypt_blocks(key, Ph, n, Cb, j[0], j[1]), jobs))
+    assert oracle_mt.first_difference(host(Cd[lo:hi]), Cb[lo:hi]) == -1
+    assert oracle_mt.first_difference(host(Cd[n + T * b0:n + T * b1]), Cb[n + T * b0:n + T * b1]) == -1
     del Ph, Cb
     st, back = ctx.decrypt(pw, Cd)
     assert st == lc.LC_OK

@@ -130,6 +130,14 @@ class FakeBackend:
     def read(self, blk, n):
         return np.zeros(n, dtype=np.uint8)
 
+    def capture_reserve(self, nbytes):
+        self.cap_left = nbytes
+
+    def capture_async(self, s, blk, n):
+        assert 0 <= blk[0] and blk[0] + n <= self.arena.cap and n <= self.cap_left
+        self.cap_left -= n
+        return np.zeros(n, dtype=np.uint8)
+
     def equals_pool(self, blk, n, off):
         return True
 
@@ -243,21 +251,45 @@ def test_serving_rejects_requests_larger_than_the_pool():
         _serve_fake(spec, pool_bytes=1 << 20)
 
 
-def _small_spec(rate=2000.0, duration=1.5, lo=256, hi=256 << 10, tamper=0.05):
+def _small_spec(rate=2000.0, duration=1.5, lo=256, hi=16 << 20, tamper=0.05):
     s = synth.cfg5_spec(rate=rate, duration=duration, lo=lo, hi=hi, tamper_frac=tamper)
     return s
 
 
+def test_capture_sample_spans_size_classes():
+    w = serve.Workload(synth.cfg5_spec(rate=20000.0, duration=2.0))
+    pick = serve.capture_sample(w, 8)
+    assert pick == sorted(set(pick)) and all(w.kind[i] == 0 for i in pick)
+    cls = {serve.size_class(int(w.size[i])) for i in pick}
+    # 256 B - 16 MiB: class 0 (<= 256 B) and the classes (2^(7+c), 2^(8+c)], c = 1..16
+    assert cls == set(range(0, 17)), sorted(cls)
+    assert serve.capture_sample(w, 8) == pick  # seeded
+
+
+def test_capture_on_fake_backend_holds_blocks():
+    spec = synth.cfg5_spec(rate=800.0, duration=0.5, lo=256, hi=1 << 20, tamper_frac=0.05)
+    be = FakeBackend(budget_bytes=256 << 20, pool_bytes=2 << 20, gbps=5.0)
+    srv = serve.Server(backend=be)
+    w = serve.Workload(spec)
+    pick = serve.capture_sample(w, 4)
+    st = srv.run(w, capture=pick, poll=0.0001)
+    assert st["completed"] == w.n and set(st["captured"]) == set(pick)
+    assert be.arena.in_use == 0 and be.cap_left == 0
+
+
 @pytest.mark.gpu
-def test_served_workload_verdicts_and_alone_vs_mix():
+def test_served_workload_verdicts_oracle_and_alone_vs_mix():
+    # Sizes 256 B - 16 MiB as in the served configuration.  All verdicts,
+    # every decrypted plaintext, and a sample of encryptions spread over every
+    # size class: byte for byte against the oracle (plaintexts regenerated on
+    # the host from the pool's seed) and against the same request run alone.
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    import oracle as O
+    import oracle_mt
     w = serve.Workload(_small_spec())
-    enc = np.flatnonzero(w.kind == 0)
-    capture = set(int(i) for i in enc[:: max(1, enc.size // 40)])
-    srv = serve.Server(0, streams=3, budget_bytes=2 << 30, pool_bytes=64 << 20,
-                       max_batch_bytes=32 << 20, max_batch_requests=1024)
+    capture = serve.capture_sample(w, 8)
+    srv = serve.Server(0, streams=3, budget_bytes=4 << 30, pool_bytes=64 << 20,
+                       max_batch_bytes=64 << 20, max_batch_requests=1024)
     try:
         st = srv.run(w, capture=capture, verify_every=1)
         assert st["completed"] == w.n
@@ -266,15 +298,19 @@ def test_served_workload_verdicts_and_alone_vs_mix():
         assert st["encrypts_ok"] == int((w.kind == 0).sum())
         assert st["plaintext_mismatches"] == 0 and st["plaintext_checked"] > 100
         assert st["batches"] > 3 and st["p99_ms"] >= st["p50_ms"] > 0
-        # each captured encryption equals the same request run alone
+        assert len(capture) >= 100 and max(w.size[capture]) > (8 << 20)
+        msgs, offs = [], []
+        for i in capture:
+            n = int(w.size[i])
+            off = srv.plain_offset(w, i, n)
+            offs.append(off)
+            msgs.append((w.pw(i), synth.uniform_bytes(srv.be.pool_seed, n, off)))
+        want = oracle_mt.encrypt_many(msgs)
         with lc.Context(0) as ctx:
-            for i in sorted(capture):
+            for k, i in enumerate(capture):
                 n = int(w.size[i])
-                off = srv.plain_offset(w, i, n)
-                alone = ctx.encrypt(w.pw(i), srv.be.pool[off:off + n]).cpu().numpy()
-                assert np.array_equal(st["captured"][i], alone), i
-                if n <= 16384:
-                    P = srv.be.pool[off:off + n].cpu().numpy()
-                    assert np.array_equal(alone, O.encrypt(w.pw(i), P)), i
+                assert np.array_equal(st["captured"][i], want[k]), (i, n)
+                alone = ctx.encrypt(w.pw(i), srv.be.pool[offs[k]:offs[k] + n]).cpu().numpy()
+                assert np.array_equal(alone, want[k]), (i, n)
     finally:
         srv.close()
