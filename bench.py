@@ -741,8 +741,9 @@ def main():
     default_launch = lc.lc_ctx_get_launch(ctx.handle).as_dict()
     tuning = None
     if not args.no_tune:
+        # tuned on a probe batch of the workload's shape and size
         t0 = time.perf_counter()
-        lc.lc_tune(ctx.handle, 0, stream)
+        lc.lc_tune(ctx.handle, int(sizes.sum()), stream)
         tuning = {"default": default_launch, "seconds": time.perf_counter() - t0,
                   "candidates": [dict(l, median_ms=ms) for l, ms in lc.lc_tune_report(ctx.handle)]}
     launch = lc.lc_ctx_get_launch(ctx.handle)

@@ -77,6 +77,11 @@ typedef struct {
   uint32_t block_len;      /* bytes per part (Sec. 5), 16..2^24, multiple of 16 */
   uint32_t tag_len;        /* integrity bytes per part, 1..8 */
   double eta;              /* offset between consecutive parts' r_0 */
+  uint32_t omega_alpha_shift; /* Sec. 3.2 Step 3 moves Omega_i with alpha_j,
+                                 j = [(i+2) mod 3]+1: 0 reads i as 1-based
+                                 (j = i, the default), 1 as 0-based (a
+                                 cyclic shift); 1 runs the FP64-pipe kernel */
+  uint32_t reserved;       /* must be 0 */
 } lc_params;
 
 typedef struct lc_ctx lc_ctx;
@@ -175,6 +180,31 @@ typedef struct {
 lc_status lc_run_batch(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_dev,
                        lc_mode m, void* stream);
 
+/* Key material beyond the password (Sec. 3.1): lambda, the offset of the
+ * starting point r_0 = a' + lambda (Eq. 5), and k, the range of Omega_i
+ * (Eq. 7).  The paper leaves both to be chosen within stated ranges, so they
+ * belong to the secret like the password.  A request of lc_run_batch_ex
+ * carries them when key_flags has LC_KEY_LAMBDA / LC_KEY_K; otherwise the
+ * context's parameters apply.  Valid values are those of Sec. 3.1:
+ * -15.67 < lambda_1 < 16.01, -11.28 < lambda_2 < 16.01,
+ * 0.090 < lambda_3 < 62.000, and 2 < k_i <= floor((52 - 14) / 8) = 4;
+ * anything else gives the request LC_ERR_ARG. */
+#define LC_KEY_LAMBDA 1u
+#define LC_KEY_K 2u
+typedef struct {
+  lc_req req;
+  uint32_t key_flags; /* LC_KEY_LAMBDA | LC_KEY_K */
+  uint32_t k[3];
+  double lambda[3];
+} lc_req_ex;
+
+/* lc_run_batch with per-request key material: the same call, results and
+ * errors, for lc_req_ex requests.  Requests of one batch may mix lambda and
+ * k values; a batch in which some request's k is not (4, 4, 4) runs the
+ * kernel variant that keeps all binary64 work on the FP64 pipe. */
+lc_status lc_run_batch_ex(lc_ctx* ctx, const lc_req_ex* reqs, size_t count, int32_t* status_dev,
+                          lc_mode m, void* stream);
+
 /* lc_run_batch with HOST buffers: `in` / `out` are host pointers (pinned
  * memory gives the best copy rate) and status_host is host memory.  The
  * library copies the inputs to its own device staging area (one copy per
@@ -250,8 +280,9 @@ lc_status lc_ctx_set_launch(lc_ctx* ctx, const lc_launch* l);
  * receives it.  The probe batch has the shape of a batched workload:
  * messages of log-uniform sizes between 1 KiB and 4 MiB (seeded, device-
  * generated bytes, distinct passwords, all encrypted in parallel mode)
- * totalling `probe_bytes` (0 = enough 4096-byte parts to fill the default
- * persistent grid twice).  Candidates: threads per CTA in {64, 128, 256},
+ * totalling `probe_bytes` (0 = enough parts to fill the largest candidate
+ * persistent grid four times; pass the size of a typical batch to tune for
+ * it).  Candidates: threads per CTA in {64, 128, 256},
  * all resident CTAs per SM or one fewer, each with the default and the
  * dense build (lc_launch.dense_build); each candidate runs once untimed and
  * three times timed with CUDA events on `stream`, and the median counts.
@@ -296,6 +327,9 @@ lc_status lc_key_info(const lc_params* p, const uint8_t* pw, size_t pw_len, lc_k
  * requests need.  Needs no GPU. */
 lc_status lc_plan_batch(const lc_params* p, const lc_req* reqs, size_t count, lc_mode m,
                         int32_t* init_status, uint64_t* nrows);
+/* The same for lc_req_ex requests (their key material is checked too). */
+lc_status lc_plan_batch_ex(const lc_params* p, const lc_req_ex* reqs, size_t count, lc_mode m,
+                           int32_t* init_status, uint64_t* nrows);
 
 /* Measured issue rates (results per second / 1e9) of the SM pipes the cipher
  * uses, from throughput microbenchmarks on `device` (not part of the paper's
@@ -379,7 +413,9 @@ uint32_t lc_emu_mask(void);
  * S = -sum p_i log2 p_i follows from it) and the sums behind the
  * auto-correlation of Fig. 3, all exact integers: sum x_i, sum x_i^2 and,
  * for k = 1..max_lag (max_lag <= LC_STATS_MAX_LAG), sum_{i < n-k} x_i x_{i+k}.
- * Uses the context's workspace; synchronises `stream`. */
+ * Uses the context's workspace; synchronises `stream`.  LC_ERR_TIMEOUT if a
+ * bounded wait of the kernel on its own asynchronous copies gave up (the
+ * results are then not valid). */
 #define LC_STATS_MAX_LAG 8
 typedef struct {
   uint64_t n;
@@ -389,6 +425,30 @@ typedef struct {
 } lc_byte_stats_t;
 lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t max_lag,
                         lc_byte_stats_t* out, void* stream);
+
+/* Digit statistics of the trajectory coordinates, Fig. 1 (Sec. 3.1): after
+ * the Euler step(s) of every byte step (body and tag bytes, both
+ * directions) of every trajectory a batch runs, each coordinate v of r is
+ * counted by its sign-magnitude decimal expansion:
+ *   int_part[c][trunc(v) + 64]   (trunc toward zero, clamped to 0..127),
+ *   digits[c][j][floor(RN(|v| 10^(2j+2))) mod 100]   for the decimal digit
+ *                                pairs 1-2 (j = 0), 3-4 (j = 1), 5-6 (j = 2),
+ * or, when |v| >= 2^31 or v is NaN, in out_of_range[c] only; c = 0, 1, 2 for
+ * x, y, z.  states = the byte steps counted.
+ *
+ * lc_ctx_digit_stats(ctx, 1) zeroes the counters and makes the context's
+ * later batches count (they then run a counting build of the FP64-pipe or
+ * v1 kernel, with identical outputs); 0 stops counting.  Synchronises the
+ * device.  lc_ctx_get_digit_stats synchronises the device and reads the
+ * counts accumulated since the last enable (all zero if never enabled). */
+typedef struct {
+  uint64_t states;
+  uint64_t int_part[3][128];
+  uint64_t digits[3][3][100];
+  uint64_t out_of_range[3];
+} lc_digit_stats_t;
+lc_status lc_ctx_digit_stats(lc_ctx* ctx, int enable);
+lc_status lc_ctx_get_digit_stats(lc_ctx* ctx, lc_digit_stats_t* out);
 
 /* Seeded input generator (not part of the paper's method): writes bytes
  * [offset, offset + n) of the counter-based SplitMix64 byte stream `seed`

@@ -36,6 +36,8 @@ class Params(C.Structure):
         ("block_len", C.c_uint32),
         ("tag_len", C.c_uint32),
         ("eta", C.c_double),
+        ("omega_alpha_shift", C.c_uint32),
+        ("reserved", C.c_uint32),
     ]
 
 
@@ -74,7 +76,16 @@ class Stats(C.Structure):
         ("max_abs_r", C.c_double),
         ("r1_hist", C.c_uint64 * 256),
         ("steps", C.c_uint64),
+        ("int_part", (C.c_uint64 * 128) * 3),
+        ("digits", ((C.c_uint64 * 100) * 3) * 3),
+        ("out_of_range", C.c_uint64 * 3),
     ]
+
+    def digit_arrays(self):
+        """(int_part [3, 128], digits [3, 3, 100], out_of_range [3]) as numpy."""
+        ip = np.array([list(self.int_part[c]) for c in range(3)], dtype=np.uint64)
+        dg = np.array([[list(self.digits[c][j]) for j in range(3)] for c in range(3)], dtype=np.uint64)
+        return ip, dg, np.array(list(self.out_of_range), dtype=np.uint64)
 
 
 _lib = None

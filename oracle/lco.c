@@ -55,11 +55,14 @@ void lco_params_v1(lco_params* p) {
   p->block_len = 4096;
   p->tag_len = 8;
   p->eta = 0x1p-24;
+  p->omega_alpha_shift = 0; /* reading R14 */
+  p->reserved = 0;
 }
 
 int lco_params_check(const lco_params* p) {
   int i;
   if (p->block_len == 0 || p->tag_len == 0 || p->tag_len > 8) return LCO_ERR_ARG;
+  if (p->omega_alpha_shift > 1) return LCO_ERR_ARG;
   for (i = 0; i < 3; i++)
     if (p->k[i] < 1 || p->k[i] > 8) return LCO_ERR_ARG;
   /* Theta divides by 10^(3 + Omega_3): Omega_3 <= 7 keeps it in TEN[]. */
@@ -303,11 +306,34 @@ void lco_block_begin(const lco_params* p, const lco_key* K, uint64_t b,
   }
 }
 
+/* Fig. 1 (Sec. 3.1): the integer part and the decimal digit pairs 1-2, 3-4
+ * and 5-6 of a coordinate, read from its sign-magnitude decimal expansion:
+ * trunc(v), and floor(|v| 10^(2j+2)) mod 100 with the product rounded once. */
+static void count_digits(lco_stats* stats, int c, double v) {
+  static const double scale[3] = {1e2, 1e4, 1e6};
+  double a = fabs(v);
+  int j, ip;
+  if (!(a < 2147483648.0)) { /* also NaN */
+    stats->out_of_range[c]++;
+    return;
+  }
+  ip = (int)v; /* toward zero */
+  ip += 64;
+  if (ip < 0) ip = 0;
+  if (ip > 127) ip = 127;
+  stats->int_part[c][ip]++;
+  for (j = 0; j < 3; j++) {
+    uint64_t u = (uint64_t)floor(a * scale[j]);
+    stats->digits[c][j][u % 100u]++;
+  }
+}
+
 static void stats_r(lco_stats* stats, const double r[3]) {
   int j;
   for (j = 0; j < 3; j++) {
     double m = fabs(r[j]);
     if (isnan(m) || m > stats->max_abs_r) stats->max_abs_r = m; /* NaN sticks */
+    count_digits(stats, j, r[j]);
   }
 }
 
@@ -344,14 +370,17 @@ uint32_t lco_step_byte(const lco_params* p, const lco_key* K, lco_state* st,
   /* Step 3 (reading R13 for the order):
    *   mu_i    <- (mu_i + R(alpha_i, Omega_i)) mod 3     old alpha, old Omega
    *   alpha_i <- r[mu_i]                                Eq. 6, new mu
-   *   Omega_i <- (Omega_i + R(alpha_i, Omega_i)) mod k_i  new alpha, old Omega
-   *            (the index [(i+2) mod 3]+1 equals i, reading R14)
+   *   Omega_i <- (Omega_i + R(alpha_j, Omega_i)) mod k_i  new alpha, old Omega
+   *            j = [(i+2) mod 3]+1: with 1-based i that is i (reading R14,
+   *            the default); with 0-based i (omega_alpha_shift = 1) it is
+   *            the cyclic predecessor of i
    *   r       <- r + a'                                                   */
   for (i = 0; i < 3; i++)
     st->mu[i] = (st->mu[i] + lco_rbyte(st->alpha[i], st->omega[i])) % 3u;
   for (i = 0; i < 3; i++) st->alpha[i] = st->r[st->mu[i]];
   for (i = 0; i < 3; i++)
-    st->omega[i] = (st->omega[i] + lco_rbyte(st->alpha[i], st->omega[i])) % p->k[i];
+    st->omega[i] = (st->omega[i] + lco_rbyte(st->alpha[p->omega_alpha_shift ? (i + 2) % 3 : i],
+                                             st->omega[i])) % p->k[i];
   for (i = 0; i < 3; i++) st->r[i] = st->r[i] + K->aprime[i];
 
   return y;

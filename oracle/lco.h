@@ -70,6 +70,10 @@ typedef struct {
   uint32_t block_len;      /* bytes per parallel part (Sec. 5) */
   uint32_t tag_len;        /* integrity bytes per part (Sec. 2) */
   double eta;              /* per-part offset of the starting point */
+  uint32_t omega_alpha_shift; /* Step 3's alpha index [(i+2) mod 3]+1 read with
+                                 1-based i (0: alpha_i) or 0-based i (1: a
+                                 cyclic shift); reading R14 */
+  uint32_t reserved;
 } lco_params;
 
 /* Key material derived from the password (Sec. 3.1, Eqs. 2-7). */
@@ -89,11 +93,20 @@ typedef struct {
   uint32_t omega[3];
 } lco_state;
 
-/* Optional run statistics (used by the chaos gate test only). */
+/* Optional run statistics: the chaos gate, and the digit statistics of the
+ * trajectory coordinates of Fig. 1 (Sec. 3.1).  After the Euler step(s) of
+ * every byte (body and tag), each coordinate v of r is counted with
+ *   int_part[c][trunc(v) + 64]  (trunc toward zero, clamped to 0..127),
+ *   digits[c][j][floor(RN(|v| 10^(2j+2))) mod 100]  for the decimal digit
+ *                               pairs 1-2, 3-4 and 5-6 (j = 0, 1, 2),
+ * or, when |v| >= 2^31 or v is NaN, in out_of_range[c] only. */
 typedef struct {
   double max_abs_r;       /* max |r_j| seen after any Euler step */
   uint64_t r1_hist[256];  /* histogram of R_nu(alpha_1, Omega_1) */
   uint64_t steps;         /* bytes processed */
+  uint64_t int_part[3][128];
+  uint64_t digits[3][3][100];
+  uint64_t out_of_range[3];
 } lco_stats;
 
 void lco_params_v1(lco_params* p);

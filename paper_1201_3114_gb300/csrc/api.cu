@@ -24,7 +24,8 @@ int kernel_variant(const DevParams& p);
 size_t batch_kernel_smem(int variant);
 const void* batch_kernel_ptr(int variant);
 cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
-                         const DevParams& p, const double* theta, cudaStream_t s);
+                         const DevParams& p, const double* theta, cudaStream_t s,
+                         unsigned long long* dig = nullptr);
 cudaError_t launch_finalize(int grid, const uint8_t* ws, const uint32_t* scratch, uint32_t block_len,
                             cudaStream_t s);
 cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offset, cudaStream_t s);
@@ -85,6 +86,8 @@ struct lc_ctx {
   int32_t* status_tmp_dev = nullptr;
   size_t status_tmp_cap = 0;
   unsigned long long* stats_dev = nullptr;  // lc_byte_stats accumulators
+  bool digits = false;                      // count the Fig. 1 digit statistics
+  unsigned long long* digits_dev = nullptr;  // 3 * kDigBins counters
   cudaStream_t copy_in = nullptr, copy_out = nullptr;  // host-buffer batch copies
   HostSlot hslots[LC_HOST_INFLIGHT];
   uint64_t next_ticket = 1;
@@ -164,6 +167,7 @@ void to_dev_params(const lc_params& p, DevParams* d) {
   d->tag_len = p.tag_len;
   for (int i = 0; i < 3; i++) d->k[i] = p.k[i];
   d->k_all4 = (p.k[0] == 4 && p.k[1] == 4 && p.k[2] == 4) ? 1u : 0u;
+  d->omega_alpha_shift = p.omega_alpha_shift;
 }
 
 size_t nblocks_of(const lc_params& p, size_t n, lc_mode m) {
@@ -305,7 +309,8 @@ lc_status build_graph(lc_ctx* ctx, int v) {
   cudaError_t e = cudaMemsetAsync(ctx->scratch_dev, 0, (4 + ctx->fail_cap) * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.a, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
-    e = launch_batch(v, G.grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams, ctx->theta_dev, s);
+    e = launch_batch(v, G.grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams, ctx->theta_dev, s,
+                     ctx->digits_dev);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.b, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
     e = launch_finalize(kFinalizeGrid, ctx->ws_dev, ctx->scratch_dev, ctx->params.block_len, s);
@@ -347,7 +352,11 @@ lc_status build_graph(lc_ctx* ctx, int v) {
 
 // Kernel variant for a batch of nrows parts: v1 batches that cannot fill
 // the GPU run the latency variant.
-int batch_variant(const lc_ctx* ctx, size_t nrows) {
+int batch_variant(const lc_ctx* ctx, size_t nrows, bool msg_k = false) {
+  // a request with its own k other than (4, 4, 4) needs the general path,
+  // which reads k per message
+  if (msg_k) return ctx->digits ? kVariantGeneralDigits : kVariantGeneral;
+  if (ctx->digits) return ctx->variant == kVariantV1 ? kVariantV1Digits : kVariantGeneralDigits;
   if (ctx->variant != kVariantV1) return ctx->variant;
   const uint64_t thr = ctx->launch.small_batch_rows ? ctx->launch.small_batch_rows
                                                     : (uint64_t)ctx->sm_count * kSmallBatchRowsPerSm;
@@ -379,25 +388,43 @@ int32_t validate_req(const lc_params& p, const lc_req& r, lc_mode m, size_t* n_o
 }
 
 
+// Per-request key material (lc_req_ex): lambda inside the ranges Sec. 3.1
+// gives for Eq. 5, k with 2 < k_i <= floor((52 - 14) / 8) = 4 (Eq. 7).
+int32_t validate_key_ex(const lc_req_ex& e) {
+  if (e.key_flags & ~(uint32_t)(LC_KEY_LAMBDA | LC_KEY_K)) return LC_ERR_ARG;
+  if (e.key_flags & LC_KEY_LAMBDA) {
+    const double lo[3] = {-15.67, -11.28, 0.090}, hi[3] = {16.01, 16.01, 62.0};
+    for (int j = 0; j < 3; j++)
+      if (!(e.lambda[j] > lo[j] && e.lambda[j] < hi[j])) return LC_ERR_ARG;
+  }
+  if (e.key_flags & LC_KEY_K)
+    for (int j = 0; j < 3; j++)
+      if (e.k[j] < 3 || e.k[j] > 4) return LC_ERR_ARG;
+  return LC_OK;
+}
+
 // Validate the requests, build the message and part tables (parts sorted
 // longest first so warps hold parts of equal length), upload them and
-// replay the graph on `s`.
+// replay the graph on `s`.  ex (optional) gives each request's own key
+// material; then reqs is ignored.
 lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* status_dev,
-                         lc_mode m, cudaStream_t s) {
+                         lc_mode m, cudaStream_t s, const lc_req_ex* ex = nullptr) {
   const lc_params& p = ctx->params;
   ctx->h_msgs.resize(count);
   ctx->h_init.resize(count);
   ctx->h_rows.clear();
   size_t full_rows = 0;
   std::vector<DevRow> partial;
+  bool msg_k = false;  // some request's k differs from (4, 4, 4)
 
   for (size_t i = 0; i < count; i++) {
-    const lc_req& r = reqs[i];
+    const lc_req& r = ex ? ex[i].req : reqs[i];
     DevMsg& M = ctx->h_msgs[i];
     memset(&M, 0, sizeof M);
     size_t n = 0;
     const HostKey* key = nullptr;
     int32_t init = validate_req(p, r, m, &n);
+    if (init == LC_OK && ex) init = validate_key_ex(ex[i]);
     if (init == LC_OK) {
       lc_status ks = get_key(ctx, r.pw, r.pw_len, &key);
       if (ks != LC_OK) init = ks;
@@ -407,13 +434,22 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
     M.in = r.in;
     M.out = r.out;
     M.n = n;
+    const bool own_lam = ex && (ex[i].key_flags & LC_KEY_LAMBDA);
+    const bool own_k = ex && (ex[i].key_flags & LC_KEY_K);
     for (int j = 0; j < 3; j++) {
-      M.base[j] = key->aprime[j] + p.lambda[j];  // one rounding, Eq. 5
+      const double lam = own_lam ? ex[i].lambda[j] : p.lambda[j];
+      M.base[j] = key->aprime[j] + lam;  // one rounding, Eq. 5
       M.aprime[j] = key->aprime[j];
     }
-    M.key_bits = key->mu[0] | key->mu[1] << 2 | key->mu[2] << 4 | key->omega[0] << 8 |
-                 key->omega[1] << 12 | key->omega[2] << 16;
+    uint32_t om[3];
+    for (int j = 0; j < 3; j++) om[j] = own_k ? key->omega_mod[j][ex[i].k[j]] : key->omega[j];
+    M.key_bits = key->mu[0] | key->mu[1] << 2 | key->mu[2] << 4 | om[0] << 8 | om[1] << 12 | om[2] << 16;
     M.flags = (r.dir == LC_DECRYPT ? kFlagDecrypt : 0u) | (m == LC_SEQUENTIAL ? kFlagSequential : 0u);
+    if (own_k) {
+      M.key_bits |= ex[i].k[0] << 20 | ex[i].k[1] << 24 | ex[i].k[2] << 28;
+      M.flags |= kFlagMsgK;
+      if (ex[i].k[0] != 4 || ex[i].k[1] != 4 || ex[i].k[2] != 4) msg_k = true;
+    }
     const size_t nb = nblocks_of(p, n, m);
     if (nb > 0xFFFFFFFFull) return LC_ERR_ARG;
     for (size_t b = 0; b < nb; b++) {
@@ -443,7 +479,7 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
                        count * sizeof(int32_t);
 
   // Device workspace (graphs are rebuilt whenever a buffer moves).
-  const int v = batch_variant(ctx, nrows);
+  const int v = batch_variant(ctx, nrows, msg_k);
   bool changed = false;
   lc_status st = grow_device(&ctx->ws_dev, &ctx->ws_cap, bytes, &changed);
   if (st != LC_OK) return st;
@@ -614,6 +650,8 @@ lc_status lc_params_default(lc_params* out) {
   out->block_len = 4096;
   out->tag_len = 8;
   out->eta = 1.0 / 16777216.0;
+  out->omega_alpha_shift = 0;
+  out->reserved = 0;
   return LC_OK;
 }
 
@@ -683,6 +721,7 @@ void lc_ctx_destroy(lc_ctx* ctx) {
     if (h.done) cudaEventDestroy(h.done);
   }
   if (ctx->stats_dev) cudaFree(ctx->stats_dev);
+  if (ctx->digits_dev) cudaFree(ctx->digits_dev);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
   if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
@@ -726,6 +765,15 @@ lc_status lc_run_batch(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t* s
   if (count == 0) return LC_OK;
   DeviceGuard g(ctx->device);
   return run_batch_impl(ctx, reqs, count, status_dev, m, static_cast<cudaStream_t>(stream));
+}
+
+lc_status lc_run_batch_ex(lc_ctx* ctx, const lc_req_ex* reqs, size_t count, int32_t* status_dev,
+                          lc_mode m, void* stream) {
+  if (!ctx || (!reqs && count) || (!status_dev && count)) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  if (count == 0) return LC_OK;
+  DeviceGuard g(ctx->device);
+  return run_batch_impl(ctx, nullptr, count, status_dev, m, static_cast<cudaStream_t>(stream), reqs);
 }
 
 lc_status lc_encrypt(lc_ctx* ctx, const uint8_t* pw, size_t pw_len, const uint8_t* P_dev, size_t n,
@@ -1026,9 +1074,15 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const lc_params& p = ctx->params;
-  const int tune_variant = ctx->variant == kVariantV1 ? kVariantV1 : ctx->variant;
-  if (probe_bytes == 0)  // two waves of the default persistent grid, in parts
-    probe_bytes = (size_t)2 * ctx->sm_count * resident_ctas(tune_variant, 256) * 256 * p.block_len;
+  const bool v1 = ctx->variant == kVariantV1;
+  if (probe_bytes == 0) {
+    // four waves, in parts, of the largest persistent grid among the
+    // candidates, so that no candidate is timed on a partly filled wave
+    int most = 0;
+    for (int v : {ctx->variant, v1 ? kVariantV1Dense : ctx->variant})
+      for (int tpc : {64, 128, 256}) most = std::max(most, resident_ctas(v, tpc) * tpc);
+    probe_bytes = (size_t)4 * ctx->sm_count * most * p.block_len;
+  }
 
   // Probe messages: log-uniform sizes in [1 KiB, 4 MiB] from a SplitMix64
   // counter stream, until probe_bytes are covered.
@@ -1076,7 +1130,6 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e0));
   if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e1));
-  const bool v1 = ctx->variant == kVariantV1;
   for (uint32_t dense = 0; dense <= (v1 ? 1u : 0u) && st == LC_OK; dense++) {
     for (uint32_t tpc : {64u, 128u, 256u}) {
       if (st != LC_OK) break;
@@ -1163,6 +1216,8 @@ lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t
   unsigned long long acc[kWords];
   LC_CUDA(cudaMemcpyAsync(acc, ctx->stats_dev, sizeof acc, cudaMemcpyDeviceToHost, s));
   LC_CUDA(cudaStreamSynchronize(s));
+  ctx->launches += 1;
+  if (acc[256]) return LC_ERR_TIMEOUT;  // a bounded wait of the kernel gave up
   out->n = n;
   // the sums follow exactly from the histogram: sum b * count, sum b^2 * count
   out->sum = 0;
@@ -1173,7 +1228,43 @@ lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t
     out->sum_sq += (uint64_t)b * (uint64_t)b * acc[b];
   }
   for (int k = 0; k < LC_STATS_MAX_LAG; k++) out->lag_sum[k] = (uint32_t)k < max_lag ? acc[258 + k] : 0;
-  ctx->launches += 1;
+  return LC_OK;
+}
+
+lc_status lc_ctx_digit_stats(lc_ctx* ctx, int enable) {
+  if (!ctx) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  if (enable) {
+    const size_t bytes = 3 * kDigBins * sizeof(unsigned long long);
+    if (!ctx->digits_dev) {
+      LC_CUDA(cudaDeviceSynchronize());
+      LC_CUDA(cudaMalloc(&ctx->digits_dev, bytes));
+      invalidate_graphs(ctx);  // the counting variants take this pointer
+    }
+    LC_CUDA(cudaDeviceSynchronize());
+    LC_CUDA(cudaMemset(ctx->digits_dev, 0, bytes));
+  }
+  ctx->digits = enable != 0;
+  return LC_OK;
+}
+
+lc_status lc_ctx_get_digit_stats(lc_ctx* ctx, lc_digit_stats_t* out) {
+  if (!ctx || !out) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  memset(out, 0, sizeof *out);
+  if (!ctx->digits_dev) return LC_OK;
+  unsigned long long h[3 * kDigBins];
+  LC_CUDA(cudaDeviceSynchronize());
+  LC_CUDA(cudaMemcpy(h, ctx->digits_dev, sizeof h, cudaMemcpyDeviceToHost));
+  for (int c = 0; c < 3; c++) {
+    const unsigned long long* hc = h + c * kDigBins;
+    for (int b = 0; b < 128; b++) out->int_part[c][b] = hc[b];
+    for (int j = 0; j < 3; j++)
+      for (int d = 0; d < 100; d++) out->digits[c][j][d] = hc[128 + 100 * j + d];
+    out->out_of_range[c] = hc[428];
+  }
+  for (int b = 0; b < 128; b++) out->states += out->int_part[0][b];
+  out->states += out->out_of_range[0];
   return LC_OK;
 }
 
@@ -1192,6 +1283,24 @@ lc_status lc_key_info(const lc_params* p, const uint8_t* pw, size_t pw_len, lc_k
   }
   out->L = k.L;
   out->D = k.D;
+  return LC_OK;
+}
+
+lc_status lc_plan_batch_ex(const lc_params* p, const lc_req_ex* reqs, size_t count, lc_mode m,
+                           int32_t* init_status, uint64_t* nrows) {
+  if ((!reqs || !init_status) && count) return LC_ERR_ARG;
+  if (m != LC_PARALLEL && m != LC_SEQUENTIAL) return LC_ERR_ARG;
+  lc_params prm;
+  if (p) prm = *p; else lc_params_default(&prm);
+  if (!params_valid(prm)) return LC_ERR_ARG;
+  uint64_t rows = 0;
+  for (size_t i = 0; i < count; i++) {
+    size_t n = 0;
+    init_status[i] = validate_req(prm, reqs[i].req, m, &n);
+    if (init_status[i] == LC_OK) init_status[i] = validate_key_ex(reqs[i]);
+    if (init_status[i] == LC_OK) rows += nblocks_of(prm, n, m);
+  }
+  if (nrows) *nrows = rows;
   return LC_OK;
 }
 

@@ -121,6 +121,41 @@ __device__ __forceinline__ uint64_t floor_scaled_hw(double alpha) {
 }
 
 // ---------------------------------------------------------------------------
+// Fig. 1 (Sec. 3.1): the integer part and the decimal digit pairs 1-2, 3-4
+// and 5-6 of a trajectory coordinate v, from its sign-magnitude decimal
+// expansion: trunc(v) + 64 (clamped to 0..127) and floor(RN(|v| 10^(2j+2)))
+// mod 100; |v| >= 2^31 or NaN is only counted as out of range.  Counted
+// into the CTA's shared histogram, layout per coordinate c:
+// [c * kDigBins + 0 .. 127] integer part, [+ 128 + 100 j + d] digit pair j,
+// [+ 428] out of range.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void count_digits(uint32_t* h, int c, double v) {
+  uint32_t* hc = h + c * kDigBins;
+  const double a = fabs(v);
+  if (!(a < 2147483648.0)) {
+    atomicAdd(hc + 428, 1u);
+    return;
+  }
+  const int ip = min(max(__double2int_rz(v) + 64, 0), 127);
+  atomicAdd(hc + ip, 1u);
+  const uint64_t u2 = __double2ull_rd(__dmul_rn(a, 1e2));
+  const uint64_t u4 = __double2ull_rd(__dmul_rn(a, 1e4));
+  const uint64_t u6 = __double2ull_rd(__dmul_rn(a, 1e6));
+  atomicAdd(hc + 128 + (uint32_t)(u2 % 100u), 1u);
+  atomicAdd(hc + 228 + (uint32_t)(u4 % 100u), 1u);
+  atomicAdd(hc + 328 + (uint32_t)(u6 % 100u), 1u);
+}
+
+template <bool kDig>
+__device__ __forceinline__ void count_state(uint32_t* dig, double x, double y, double z) {
+  if constexpr (kDig) {
+    count_digits(dig, 0, x);
+    count_digits(dig, 1, y);
+    count_digits(dig, 2, z);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Trajectory state between bytes (Sec. 3.2).  V_i caches floor(alpha_i
 // 10^13): alpha_i only changes in Step 3, and every R_nu of the following
 // byte reads the same V_i.
@@ -132,6 +167,7 @@ struct GeneralPath {
   double x, y, z, ax, ay, az;
   uint64_t V0, V1, V2;
   uint32_t mu0, mu1, mu2, om0, om1, om2;
+  uint32_t k0, k1, k2;  // Omega ranges (Eq. 7): the message's own or the parameters'
 
   static constexpr int kThetaRows = K4 ? 4 : kMaxK;
   static constexpr int kMinCtas = 1;
@@ -148,12 +184,19 @@ struct GeneralPath {
     return (uint32_t)(V >> (8u * om)) & 255u;
   }
   __device__ __forceinline__ static uint32_t modk(uint32_t v, uint32_t k) { return K4 ? (v & 3u) : v % k; }
+  __device__ __forceinline__ void set_k(const DevMsg& Mg, const DevParams& p) {
+    const bool own = (Mg.flags & kFlagMsgK) != 0;
+    k0 = own ? (Mg.key_bits >> 20) & 15u : p.k[0];
+    k1 = own ? (Mg.key_bits >> 24) & 15u : p.k[1];
+    k2 = own ? (Mg.key_bits >> 28) & 15u : p.k[2];
+  }
 
   // Sec. 3.2, Steps 1-3, for one byte.  dec = 0: in is P_i, returns C_i.
   // dec = 1: in is C_i, returns P_i.  The direction is data, not control
   // flow, so encrypting and decrypting threads of one warp never diverge.
+  template <bool kDig = false>
   __device__ __forceinline__ uint32_t step(uint32_t in, uint32_t dec, const DevParams& p,
-                                           const double* __restrict__ theta) {
+                                           const double* __restrict__ theta, uint32_t* dig = nullptr) {
     // Step 1 (Eqs. 9, 10): R_nu(alpha_1, Omega_1) + R_nu(alpha_2, Omega_2).
     const uint32_t R1 = rb(V0, om0), R2 = rb(V1, om1);
     const uint32_t s = R1 + R2;
@@ -165,6 +208,7 @@ struct GeneralPath {
     y = mu2 == 1 ? kicked : y;
     z = mu2 == 2 ? kicked : z;
     for (uint32_t k = 0; k < p.steps_per_byte; k++) euler_hw(x, y, z, p);
+    count_state<kDig>(dig, x, y, z);
     // Step 3: mu from the old alpha and Omega; alpha re-read from r with the
     // new mu (Eq. 6); Omega from the new alpha and the old Omega; r += a'.
     const uint32_t R3 = rb(V2, om2);
@@ -172,9 +216,13 @@ struct GeneralPath {
     mu1 = (mu1 + R2) % 3u;
     mu2 = (mu2 + R3) % 3u;
     set_alpha();
-    om0 = modk(om0 + rb(V0, om0), p.k[0]);
-    om1 = modk(om1 + rb(V1, om1), p.k[1]);
-    om2 = modk(om2 + rb(V2, om2), p.k[2]);
+    // Omega_i moves with alpha_j, j = [(i+2) mod 3]+1: i itself for 1-based
+    // i, the cyclic predecessor for 0-based i (omega_alpha_shift)
+    const bool cyc = p.omega_alpha_shift != 0;
+    const uint64_t W0 = cyc ? V2 : V0, W1 = cyc ? V0 : V1, W2 = cyc ? V1 : V2;
+    om0 = modk(om0 + rb(W0, om0), k0);
+    om1 = modk(om1 + rb(W1, om1), k1);
+    om2 = modk(om2 + rb(W2, om2), k2);
     x = __dadd_rn(x, ax);
     y = __dadd_rn(y, ay);
     z = __dadd_rn(z, az);
@@ -226,9 +274,11 @@ struct V1Path {
     }
   }
   __device__ __forceinline__ static uint32_t rb(uint32_t V, uint32_t om) { return (V >> (8u * om)) & 255u; }
+  __device__ __forceinline__ void set_k(const DevMsg&, const DevParams&) {}  // k = (4, 4, 4)
 
+  template <bool kDig = false>
   __device__ __forceinline__ uint32_t step(uint32_t in, uint32_t dec, const DevParams& p,
-                                           const double* __restrict__ theta) {
+                                           const double* __restrict__ theta, uint32_t* dig = nullptr) {
     const uint32_t R1 = rb(V0, om0), R2 = rb(V1, om1);
     const uint32_t s = R1 + R2;
     const uint32_t out = (dec ? (in - s) : (in + s)) & 255u;
@@ -238,6 +288,7 @@ struct V1Path {
     y = mu2 == 1 ? kicked : y;
     z = mu2 == 2 ? kicked : z;
     for (uint32_t k = 0; k < p.steps_per_byte; k++) euler_v1<M>(x, y, z, p.beta, p.dt);
+    count_state<kDig>(dig, x, y, z);
     const uint32_t R3 = rb(V2, om2);
     mu0 = (mu0 + R1) % 3u;
     mu1 = (mu1 + R2) % 3u;
@@ -262,9 +313,9 @@ __device__ __forceinline__ uint32_t sel4(uint32_t q, uint32_t v0, uint32_t v1, u
 // One trajectory: Eq. 5 plus the part offset b * eta, the warm-up, then the
 // part's body bytes and its tag.  Returns the tag verdict (always true when
 // encrypting).
-template <class Path>
+template <class Path, bool kDig>
 __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
-                        const double* __restrict__ theta) {
+                        const double* __restrict__ theta, uint32_t* dig) {
   const bool seq = (Mg.flags & kFlagSequential) != 0;
   const uint32_t dec = (Mg.flags & kFlagDecrypt) ? 1u : 0u;
   const uint64_t lo = seq ? 0 : (uint64_t)b * p.block_len;
@@ -286,6 +337,7 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
   t.om0 = (Mg.key_bits >> 8) & 15u;
   t.om1 = (Mg.key_bits >> 12) & 15u;
   t.om2 = (Mg.key_bits >> 16) & 15u;
+  t.set_k(Mg, p);
   t.set_alpha();
 
   const uint8_t* src = Mg.in + lo;
@@ -296,7 +348,7 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
   // Tail: single bytes.
   const uint64_t head = min((uint64_t)((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u), len);
   uint64_t i = 0;
-  for (; i < head; i++) dst[i] = (uint8_t)t.step(src[i], dec, p, theta);
+  for (; i < head; i++) dst[i] = (uint8_t)t.template step<kDig>(src[i], dec, p, theta, dig);
   const uint64_t nv = (len - head) >> 4;
   if (nv) {
     const uint8_t* s1 = src + head;
@@ -324,7 +376,7 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
       uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
 #pragma unroll 1
       for (int j = 0; j < 16; j++) {
-        const uint32_t yb = t.step(i0 & 255u, dec, p, theta);
+        const uint32_t yb = t.template step<kDig>(i0 & 255u, dec, p, theta, dig);
         i0 = __funnelshift_r(i0, i1, 8);
         i1 = __funnelshift_r(i1, i2, 8);
         i2 = __funnelshift_r(i2, i3, 8);
@@ -339,17 +391,17 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
     }
     i = head + (nv << 4);
   }
-  for (; i < len; i++) dst[i] = (uint8_t)t.step(src[i], dec, p, theta);
+  for (; i < len; i++) dst[i] = (uint8_t)t.template step<kDig>(src[i], dec, p, theta, dig);
 
   // Tag: T further bytes whose plaintext is the message length, LE64(n).
   bool ok = true;
   for (uint32_t q = 0; q < p.tag_len; q++) {
     const uint32_t Q = (uint32_t)(Mg.n >> (8 * q)) & 255u;
     if (dec) {
-      const uint32_t got = t.step(Mg.in[tag_off + q], 1u, p, theta);
+      const uint32_t got = t.template step<kDig>(Mg.in[tag_off + q], 1u, p, theta, dig);
       ok = ok && (got == Q);
     } else {
-      Mg.out[tag_off + q] = (uint8_t)t.step(Q, 0u, p, theta);
+      Mg.out[tag_off + q] = (uint8_t)t.template step<kDig>(Q, 0u, p, theta, dig);
     }
   }
   return ok;
@@ -364,14 +416,21 @@ __device__ __forceinline__ void load_msg(DevMsg& m, const DevMsg* src) {
 
 // Persistent batched kernel: CTAs stay resident and pull rows of the
 // flattened part table (sorted longest first) with warp-aggregated atomics.
-template <class Path>
+// kDig: also count the Fig. 1 digit statistics of every state after the
+// Euler step(s) of a byte into dig_g (3 * kDigBins 64-bit counters).
+template <class Path, bool kDig = false>
 __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_t* __restrict__ ws,
                                                     uint32_t* __restrict__ scratch,
                                                     DevParams p,
-                                                    const double* __restrict__ theta_g) {
+                                                    const double* __restrict__ theta_g,
+                                                    unsigned long long* __restrict__ dig_g) {
   extern __shared__ double s_theta[];
+  __shared__ uint32_t s_dig[kDig ? 3 * kDigBins : 1];
   const int nth = Path::kThetaRows * 256;
   for (int i = threadIdx.x; i < nth; i += blockDim.x) s_theta[i] = theta_g[i];
+  if constexpr (kDig) {
+    for (int i = threadIdx.x; i < 3 * kDigBins; i += blockDim.x) s_dig[i] = 0u;
+  }
   __syncthreads();
 
   const DevHeader* H = reinterpret_cast<const DevHeader*>(ws);
@@ -431,7 +490,7 @@ __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_
       }
     }
 #endif
-    const bool ok = run_row<Path>(M, row.b, p, s_theta);
+    const bool ok = run_row<Path, kDig>(M, row.b, p, s_theta, s_dig);
     if (M.flags & kFlagDecrypt) {
       // Segmented vote: threads of the warp holding parts of the same
       // message combine their verdicts; one atomic per message and warp.
@@ -440,6 +499,11 @@ __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_
       const bool any_bad = same.any(!ok);
       if (same.thread_rank() == 0 && any_bad) atomicOr(fail + row.msg, 1u);
     }
+  }
+  if constexpr (kDig) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * kDigBins; i += blockDim.x)
+      if (s_dig[i]) atomicAdd(dig_g + i, (unsigned long long)s_dig[i]);
   }
 }
 
@@ -517,13 +581,14 @@ using KV1Dense = V1Path<LC_EMU_MASK, 4>;
 // ---------------------------------------------------------------------------
 
 int kernel_variant(const DevParams& p) {
-  if (!p.k_all4) return kVariantGeneral;
+  if (!p.k_all4 || p.omega_alpha_shift) return kVariantGeneral;
   if (p.sigma == 10.0 && p.rho == 28.0) return kVariantV1;
   return kVariantGeneral4;
 }
 
 size_t batch_kernel_smem(int variant) {
-  return (variant == kVariantGeneral ? kThetaEntries : 4 * 256) * sizeof(double);
+  const bool general = variant == kVariantGeneral || variant == kVariantGeneralDigits;
+  return (general ? kThetaEntries : 4 * 256) * sizeof(double);
 }
 
 const void* batch_kernel_ptr(int variant) {
@@ -532,19 +597,36 @@ const void* batch_kernel_ptr(int variant) {
     case kVariantGeneral4: return reinterpret_cast<const void*>(&batch_kernel<KGeneral4>);
     case kVariantV1Latency: return reinterpret_cast<const void*>(&batch_kernel<KV1Lat>);
     case kVariantV1Dense: return reinterpret_cast<const void*>(&batch_kernel<KV1Dense>);
+    case kVariantV1Digits: return reinterpret_cast<const void*>(&batch_kernel<KV1, true>);
+    case kVariantGeneralDigits: return reinterpret_cast<const void*>(&batch_kernel<KGeneral, true>);
     default: return reinterpret_cast<const void*>(&batch_kernel<KV1>);
   }
 }
 
 cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
-                         const DevParams& p, const double* theta, cudaStream_t s) {
+                         const DevParams& p, const double* theta, cudaStream_t s,
+                         unsigned long long* dig) {
   const size_t smem = batch_kernel_smem(variant);
   switch (variant) {
-    case kVariantGeneral: batch_kernel<KGeneral><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
-    case kVariantGeneral4: batch_kernel<KGeneral4><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
-    case kVariantV1Latency: batch_kernel<KV1Lat><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
-    case kVariantV1Dense: batch_kernel<KV1Dense><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
-    default: batch_kernel<KV1><<<grid, block, smem, s>>>(ws, scratch, p, theta); break;
+    case kVariantGeneral:
+      batch_kernel<KGeneral><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      break;
+    case kVariantGeneral4:
+      batch_kernel<KGeneral4><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      break;
+    case kVariantV1Latency:
+      batch_kernel<KV1Lat><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      break;
+    case kVariantV1Dense:
+      batch_kernel<KV1Dense><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      break;
+    case kVariantV1Digits:
+      batch_kernel<KV1, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      break;
+    case kVariantGeneralDigits:
+      batch_kernel<KGeneral, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      break;
+    default: batch_kernel<KV1><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig); break;
   }
   return cudaGetLastError();
 }

@@ -144,6 +144,7 @@ bool params_valid(const lc_params& p) {
     if (p.k[i] < 1 || p.k[i] > 8) return false;
   if (p.block_len < 16 || p.block_len > (1u << 24) || (p.block_len % 16) != 0) return false;
   if (p.tag_len < 1 || p.tag_len > 8) return false;
+  if (p.omega_alpha_shift > 1 || p.reserved != 0) return false;
   return true;
 }
 
@@ -205,14 +206,17 @@ lc_status key_schedule(const lc_params& p, const uint8_t* pw, size_t n, HostKey*
     }
     uint8_t d[32];
     sha256(buf, sizeof buf, d);
-    uint64_t acc = 0;  // Horner over 32-bit big-endian words
-    const uint64_t kk = p.k[i - 1];
-    for (int w = 0; w < 8; w++) {
-      uint64_t word = (uint64_t)d[4 * w] << 24 | (uint64_t)d[4 * w + 1] << 16 |
-                      (uint64_t)d[4 * w + 2] << 8 | d[4 * w + 3];
-      acc = ((acc << 32) + word) % kk;
+    K.omega_mod[i - 1][0] = 0;
+    for (uint64_t kk = 1; kk <= 8; kk++) {
+      uint64_t acc = 0;  // Horner over 32-bit big-endian words
+      for (int w = 0; w < 8; w++) {
+        uint64_t word = (uint64_t)d[4 * w] << 24 | (uint64_t)d[4 * w + 1] << 16 |
+                        (uint64_t)d[4 * w + 2] << 8 | d[4 * w + 3];
+        acc = ((acc << 32) + word) % kk;
+      }
+      K.omega_mod[i - 1][kk] = (uint8_t)acc;
     }
-    K.omega[i - 1] = (uint32_t)acc;
+    K.omega[i - 1] = K.omega_mod[i - 1][p.k[i - 1]];
   }
   *out = K;
   return LC_OK;

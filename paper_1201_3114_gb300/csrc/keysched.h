@@ -15,7 +15,8 @@ struct HostKey {
   uint32_t L, D;     // L = floor(n/3); least D with 10^D >= 2^(8(L+1))
   double aprime[3];  // g(a_i)
   uint32_t mu[3];    // initial mu (Sec. 3.1)
-  uint32_t omega[3]; // Eq. 7
+  uint32_t omega[3]; // Eq. 7 with the parameters' k
+  uint8_t omega_mod[3][9];  // hash(i a) mod k for every k = 1..8 (per-request k)
 };
 
 // FIPS 180-4 SHA-256.

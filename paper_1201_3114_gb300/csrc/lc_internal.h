@@ -26,7 +26,15 @@ constexpr int kVariantV1 = 2;
 constexpr int kVariantV1Latency = 3;
 // kVariantV1 compiled for 4 resident 256-thread CTAs per SM (64 registers).
 constexpr int kVariantV1Dense = 4;
-constexpr int kNumVariants = 5;
+// kVariantV1 and kVariantGeneral that also count the digit statistics of
+// Fig. 1 (lc_ctx_digit_stats).
+constexpr int kVariantV1Digits = 5;
+constexpr int kVariantGeneralDigits = 6;
+constexpr int kNumVariants = 7;
+
+// Fig. 1 digit statistics: counters per coordinate (128 integer-part bins,
+// 3 x 100 digit-pair bins, 1 out-of-range count).
+constexpr int kDigBins = 429;
 
 // Below this many parts per SM (1.5 warps per SM sub-partition) a v1 batch
 // runs the latency variant (measured crossover on GB300).
@@ -41,6 +49,7 @@ struct DevParams {
   uint32_t tag_len;
   uint32_t k[3];
   uint32_t k_all4;  // 1 when k = (4, 4, 4): Omega fits in two bits
+  uint32_t omega_alpha_shift;  // Step 3's alpha index read with 0-based i
 };
 
 // One message of a batch, as the kernels see it (80 bytes).
@@ -50,13 +59,17 @@ struct alignas(16) DevMsg {
   uint64_t n;          // plaintext length in bytes
   double base[3];      // RN(a'_j + lambda_j): Eq. 5 without the part offset
   double aprime[3];    // a'_j, added after every byte (Step 3)
-  uint32_t key_bits;   // mu_i in bits [2i, 2i+2), Omega_i in bits [8+4i, 12+4i)
-  uint32_t flags;      // kFlagDecrypt | kFlagSequential
+  uint32_t key_bits;   // mu_i in bits [2i, 2i+2), Omega_i in bits [8+4i, 12+4i),
+                       // with kFlagMsgK: k_i in bits [20+4i, 24+4i)
+  uint32_t flags;      // kFlagDecrypt | kFlagSequential | kFlagMsgK
 };
 static_assert(sizeof(DevMsg) == 80, "DevMsg layout");
 
 constexpr uint32_t kFlagDecrypt = 1u;
 constexpr uint32_t kFlagSequential = 2u;
+// The message carries its own k (per-request key material, Eq. 7); only the
+// general kernel variant reads it.
+constexpr uint32_t kFlagMsgK = 4u;
 
 // One trajectory: part `b` of message `msg` (b = 0 in sequential mode).
 struct DevRow {

@@ -4,15 +4,20 @@
 // auto-correlation of Fig. 3.  Every quantity is an exact integer sum, so
 // the result does not depend on the order in which threads add.
 //
-// One pass over the data.  Each CTA keeps a private histogram in shared
-// memory laid out as [bin][lane]: lane l of every warp counts into column l,
-// so the 32 atomics of a warp instruction always fall in 32 different banks.
-// Threads read 32 consecutive bytes per iteration with 16-byte loads (plus
-// the next 8 bytes for the lagged products), form the sums of products four
-// bytes at a time with the unsigned 4-way byte dot product (__dp4a), and add
-// their partial sums to the global 64-bit totals once per CTA at the end.
-// The sum and the sum of squares are not accumulated here: they follow
-// exactly from the histogram (the host forms them).
+// One pass over the data, bound by HBM bandwidth.  Each CTA keeps a private
+// histogram in shared memory laid out as [bin][lane]: lane l of every warp
+// counts into column l, so the 32 atomics of a warp instruction always fall
+// in 32 different banks.  The bytes reach the CTA as whole 16 KiB tiles that
+// one thread copies from global to shared memory with bulk asynchronous
+// copies (cp.async.bulk, completion on an mbarrier), four tiles in flight
+// per CTA, so that the loads' latency is hidden behind the counting of the
+// previous tiles.  Each thread then counts two 32-byte chunks of a tile (plus
+// the next 8 bytes for the lagged products), forming the sums of products
+// four bytes at a time with the unsigned 4-way byte dot product (__dp4a);
+// the partial sums reach the global 64-bit totals once per CTA at the end.
+// The ragged end of the buffer (less than one tile) is read with guarded
+// loads.  The sum and the sum of squares are not accumulated here: they
+// follow exactly from the histogram (the host forms them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,9 +27,26 @@ namespace lc {
 
 namespace {
 
+// Chunks per thread in a staged tile and tiles in flight per CTA (chosen
+// by measurement on GB300).
+#ifndef LC_STATS_CPT
+#define LC_STATS_CPT 2
+#endif
+#ifndef LC_STATS_STAGES
+#define LC_STATS_STAGES 4
+#endif
+
 constexpr int kThreads = 256;
-constexpr uint32_t kChunk = 32;                          // bytes per thread per iteration
-constexpr uint64_t kTile = 8ull * kChunk * kThreads;     // 64 KiB per CTA per tile
+constexpr uint32_t kChunk = 32;                            // bytes per thread and count step
+constexpr int kCpt = LC_STATS_CPT;
+constexpr uint32_t kTileBytes = kCpt * kChunk * kThreads;  // bytes per staged tile
+constexpr uint32_t kCopyBytes = kTileBytes + 16;           // + the 16 bytes after it (lag partners)
+constexpr uint32_t kStageStride = kTileBytes + 128;        // keeps every stage 128-byte aligned
+constexpr int kStages = LC_STATS_STAGES;
+constexpr uint32_t kHistBytes = 256 * 32 * 4;
+constexpr size_t kSmemBytes = kHistBytes + (size_t)kStages * kStageStride;
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier waits
+constexpr int kTimeoutWord = 256;          // acc[256]: set when a wait gave up
 
 // Bytes i .. i + 3 of data as a little-endian word, 0 for bytes at or past
 // n (only for the ragged end of the buffer).
@@ -36,23 +58,108 @@ __device__ __forceinline__ uint32_t guarded_word(const uint8_t* data, uint64_t i
   return v;
 }
 
-// acc layout (uint64): [0, 256) histogram, 256 and 257 unused (zero),
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Thread 0: announce `bytes` on the barrier and start the bulk copy of
+// [src, src + bytes) into shared memory at dst.  16-byte aligned source and
+// destination, size a multiple of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier to complete; false after
+// kSpinLimit polls (each poll may itself suspend the thread for a while).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Histogram of the 32 bytes w[0..7] (all counted).
+__device__ __forceinline__ void hist_chunk(uint32_t* hl, const uint32_t (&w)[10]) {
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    // address of bin x, column lane: x * 32 + lane words
+    atomicAdd(&hl[(w[j] & 255u) << 5], 1u);
+    atomicAdd(&hl[((w[j] >> 8) & 255u) << 5], 1u);
+    atomicAdd(&hl[((w[j] >> 16) & 255u) << 5], 1u);
+    atomicAdd(&hl[(w[j] >> 24) << 5], 1u);
+  }
+}
+
+// Lagged products x_i x_{i+k}, k = 1..8, of the 32 bytes w[0..7] with their
+// 8 successors w[8], w[9], into 32-bit partials.
+__device__ __forceinline__ void lags_chunk(const uint32_t (&w)[10], uint32_t (&tl)[LC_STATS_MAX_LAG]) {
+  // sh[s][j]: the word of bytes x_{4j+s} .. x_{4j+s+3}, s = 1..3; lag k + 4
+  // reuses the shifted word of index j + 1.
+  uint32_t sh1[9], sh2[9], sh3[9];
+#pragma unroll
+  for (int j = 0; j < 9; j++) {
+    sh1[j] = __funnelshift_r(w[j], w[j + 1], 8);
+    sh2[j] = __funnelshift_r(w[j], w[j + 1], 16);
+    sh3[j] = __funnelshift_r(w[j], w[j + 1], 24);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    tl[0] = __dp4a(w[j], sh1[j], tl[0]);
+    tl[1] = __dp4a(w[j], sh2[j], tl[1]);
+    tl[2] = __dp4a(w[j], sh3[j], tl[2]);
+    tl[3] = __dp4a(w[j], w[j + 1], tl[3]);
+    tl[4] = __dp4a(w[j], sh1[j + 1], tl[4]);
+    tl[5] = __dp4a(w[j], sh2[j + 1], tl[5]);
+    tl[6] = __dp4a(w[j], sh3[j + 1], tl[6]);
+    tl[7] = __dp4a(w[j], w[j + 2], tl[7]);
+  }
+}
+
+// acc layout (uint64): [0, 256) histogram, 256 the timeout flag, 257 unused,
 // 258 + k - 1 for lag k = 1..max_lag: sum of x_i x_{i+k}.
 //
 // `data` here is 16-byte aligned; the caller's unaligned head is counted by
-// thread 0 of CTA 0 from `head` (h bytes before data).
+// thread 0 of CTA 0 from `head` (h bytes before data).  Tiles [0, ntiles)
+// of kTileBytes are staged (each with the 16 bytes after it, all inside
+// the buffer); the rest [ntiles * kTileBytes, m) is counted by the last CTA
+// with guarded loads.
 template <bool kLags>
 __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restrict__ head, uint32_t h,
                                                          const uint8_t* __restrict__ data, uint64_t m,
-                                                         uint32_t max_lag, unsigned long long* acc) {
-  __shared__ uint32_t hist[256 * 32];
+                                                         uint64_t ntiles, uint32_t max_lag,
+                                                         unsigned long long* acc) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  uint32_t* const hist = reinterpret_cast<uint32_t*>(smem);
+  uint8_t* const stage = smem + kHistBytes;
   for (int i = threadIdx.x; i < 256 * 32; i += kThreads) hist[i] = 0u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(smem_addr(&bars[s]), 1u);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
   uint32_t* const hl = hist + lane;
   uint64_t lag[LC_STATS_MAX_LAG];
+  uint32_t tl[LC_STATS_MAX_LAG];
 #pragma unroll
-  for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] = 0;
+  for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] = 0, tl[k] = 0;
 
   // The unaligned head: at most 15 bytes, each with its lagged partners,
   // which may lie in the aligned part.
@@ -72,66 +179,81 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
     }
   }
 
-  for (uint64_t base = (uint64_t)blockIdx.x * kTile; base < m; base += (uint64_t)gridDim.x * kTile) {
-    const uint64_t end = base + kTile < m ? base + kTile : m;
-    // 32-bit partial sums per tile: a thread adds 8 chunks of 32 bytes per
-    // tile, so every partial stays below 256 * 255^2 < 2^32.
-    uint32_t tl[LC_STATS_MAX_LAG];
+  // Staged tiles t = blockIdx.x + i * gridDim.x: a ring of kStages buffers,
+  // tile i in stage i mod kStages, its barrier completing phase
+  // (i / kStages) mod 2.
+  const uint64_t mine = ntiles > blockIdx.x ? (ntiles - blockIdx.x - 1) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (uint64_t i = 0; i < (uint64_t)kStages && i < mine; i++)
+      bulk_load(smem_addr(stage + i * kStageStride), data + (blockIdx.x + i * gridDim.x) * (uint64_t)kTileBytes,
+                kCopyBytes, smem_addr(&bars[i]));
+  }
+  uint64_t done = 0;
+  bool timed_out = false;
+  for (uint64_t i = 0; i < mine; i++) {
+    const int s = (int)(i % kStages);
+    const bool ok = mbar_wait(smem_addr(&bars[s]), (uint32_t)((i / kStages) & 1u));
+    if (__syncthreads_or(!ok)) {  // the whole CTA leaves together
+      timed_out = true;
+      break;
+    }
+    const uint8_t* st = stage + s * kStageStride;
 #pragma unroll
-    for (int k = 0; k < LC_STATS_MAX_LAG; k++) tl[k] = 0;
-    for (uint64_t i = base + (uint64_t)kChunk * threadIdx.x; i < end; i += (uint64_t)kChunk * kThreads) {
+    for (int c = 0; c < kCpt; c++) {
+      const uint32_t off = (threadIdx.x + c * kThreads) * kChunk;
       uint32_t w[10];
-      const bool full = i + kChunk <= end;
-      if (full) {
-        const uint4 a = *reinterpret_cast<const uint4*>(data + i);
-        const uint4 b = *reinterpret_cast<const uint4*>(data + i + 16);
-        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
-        w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+      const uint4 a = *reinterpret_cast<const uint4*>(st + off);
+      const uint4 b = *reinterpret_cast<const uint4*>(st + off + 16);
+      const uint2 n8 = *reinterpret_cast<const uint2*>(st + off + 32);
+      w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
+      w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+      w[8] = n8.x, w[9] = n8.y;
+      hist_chunk(hl, w);
+      if (kLags) lags_chunk(w, tl);
+    }
+    // 32-bit partials: one tile adds kCpt x 32 products below 2^16 per lag,
+    // so 256 / kCpt tiles stay below 2^32
+    static_assert(kCpt == 1 || kCpt == 2 || kCpt == 4, "flush period");
+    if ((i & (256u / kCpt - 1u)) == 256u / kCpt - 1u) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          // address of bin x, column lane: x * 32 + lane words
-          atomicAdd(&hl[(w[j] & 255u) << 5], 1u);
-          atomicAdd(&hl[((w[j] >> 8) & 255u) << 5], 1u);
-          atomicAdd(&hl[((w[j] >> 16) & 255u) << 5], 1u);
-          atomicAdd(&hl[(w[j] >> 24) << 5], 1u);
-        }
+      for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k], tl[k] = 0;
+    }
+    done = i + 1;
+    __syncthreads();  // every thread is done with stage s
+    if (threadIdx.x == 0 && i + kStages < mine) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_load(smem_addr(stage + s * kStageStride),
+                data + (blockIdx.x + (i + kStages) * gridDim.x) * (uint64_t)kTileBytes, kCopyBytes,
+                smem_addr(&bars[s]));
+    }
+  }
+  if (timed_out) {
+    // Record the failure and wait (bounded) for the copies still in flight
+    // before the CTA's shared memory is released.
+    if (threadIdx.x == 0) {
+      atomicOr(acc + kTimeoutWord, 1ull);
+      for (uint64_t i = done; i < mine && i < done + kStages; i++)
+        mbar_wait(smem_addr(&bars[i % kStages]), (uint32_t)((i / kStages) & 1u));
+    }
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k], tl[k] = 0;
+
+  // The rest of the buffer (< one tile + 32 bytes) on the last CTA, with
+  // guarded loads: bytes at or past m read as 0 and are not counted.
+  if (blockIdx.x == gridDim.x - 1) {
+    for (uint64_t i = ntiles * kTileBytes + (uint64_t)kChunk * threadIdx.x; i < m;
+         i += (uint64_t)kChunk * kThreads) {
+      uint32_t w[10];
+#pragma unroll
+      for (int j = 0; j < 10; j++) w[j] = guarded_word(data, i + 4 * j, m);
+      if (i + kChunk <= m) {
+        hist_chunk(hl, w);
       } else {
-        // the ragged end of the buffer: bytes at or past m read as 0 and
-        // are not counted
-#pragma unroll
-        for (int j = 0; j < 8; j++) w[j] = guarded_word(data, i + 4 * j, m);
-        for (uint32_t q = 0; q < kChunk && i + q < m; q++)
-          atomicAdd(&hl[((w[q >> 2] >> (8 * (q & 3))) & 255u) << 5], 1u);
+        for (uint32_t q = 0; i + q < m; q++) atomicAdd(&hl[((w[q >> 2] >> (8 * (q & 3))) & 255u) << 5], 1u);
       }
-      if (kLags) {
-        if (i + kChunk + 8 <= m) {
-          const uint2 c = *reinterpret_cast<const uint2*>(data + i + kChunk);
-          w[8] = c.x, w[9] = c.y;
-        } else {
-          w[8] = guarded_word(data, i + kChunk, m);
-          w[9] = guarded_word(data, i + kChunk + 4, m);
-        }
-        // sh[s][j]: the word of bytes x_{4j+s} .. x_{4j+s+3}, s = 1..3;
-        // lag k + 4 reuses the shifted word of index j + 1.
-        uint32_t sh1[9], sh2[9], sh3[9];
-#pragma unroll
-        for (int j = 0; j < 9; j++) {
-          sh1[j] = __funnelshift_r(w[j], w[j + 1], 8);
-          sh2[j] = __funnelshift_r(w[j], w[j + 1], 16);
-          sh3[j] = __funnelshift_r(w[j], w[j + 1], 24);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-          tl[0] = __dp4a(w[j], sh1[j], tl[0]);
-          tl[1] = __dp4a(w[j], sh2[j], tl[1]);
-          tl[2] = __dp4a(w[j], sh3[j], tl[2]);
-          tl[3] = __dp4a(w[j], w[j + 1], tl[3]);
-          tl[4] = __dp4a(w[j], sh1[j + 1], tl[4]);
-          tl[5] = __dp4a(w[j], sh2[j + 1], tl[5]);
-          tl[6] = __dp4a(w[j], sh3[j + 1], tl[6]);
-          tl[7] = __dp4a(w[j], w[j + 2], tl[7]);
-        }
-      }
+      if (kLags) lags_chunk(w, tl);
     }
 #pragma unroll
     for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k];
@@ -160,6 +282,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
 
 }  // namespace
 
+// acc[256] != 0 after the kernel: a bounded wait gave up (LC_ERR_TIMEOUT).
 cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsigned long long* acc,
                          int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(acc, 0, (258 + LC_STATS_MAX_LAG) * sizeof(unsigned long long), s);
@@ -168,20 +291,25 @@ cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsi
   const uint32_t h = (uint32_t)(mis ? (16u - mis < n ? 16u - mis : n) : 0u);
   const uint8_t* body = data + h;
   const uint64_t m = n - h;
-  const uint64_t tiles = (m + kTile - 1) / kTile;
-  // one wave of resident CTAs: equal shares of tiles, no second wave
+  // staged tiles: tile t and the 16 bytes after it lie inside the first
+  // m16 = m rounded down to 16 bytes
+  const uint64_t m16 = m & ~(uint64_t)15;
+  const uint64_t ntiles = m16 >= 16 ? (m16 - 16) / kTileBytes : 0;
   const void* fn = max_lag ? reinterpret_cast<const void*>(&stats_kernel<true>)
                            : reinterpret_cast<const void*>(&stats_kernel<false>);
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  // one wave of resident CTAs, at most one per tile
   uint64_t grid = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
-  if (tiles < grid) grid = tiles;
+  if (ntiles < grid) grid = ntiles;
   if (grid == 0) grid = 1;
   if (max_lag)
-    stats_kernel<true><<<(unsigned)grid, kThreads, 0, s>>>(data, h, body, m, max_lag, acc);
+    stats_kernel<true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(data, h, body, m, ntiles, max_lag, acc);
   else
-    stats_kernel<false><<<(unsigned)grid, kThreads, 0, s>>>(data, h, body, m, max_lag, acc);
+    stats_kernel<false><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(data, h, body, m, ntiles, max_lag, acc);
   return cudaGetLastError();
 }
 

@@ -41,6 +41,8 @@ class lc_params(C.Structure):
         ("block_len", C.c_uint32),
         ("tag_len", C.c_uint32),
         ("eta", C.c_double),
+        ("omega_alpha_shift", C.c_uint32),
+        ("reserved", C.c_uint32),
     ]
 
 
@@ -53,6 +55,18 @@ class lc_req(C.Structure):
         ("in_len", C.c_size_t),
         ("out", C.c_void_p),
         ("out_cap", C.c_size_t),
+    ]
+
+
+LC_KEY_LAMBDA, LC_KEY_K = 1, 2
+
+
+class lc_req_ex(C.Structure):
+    _fields_ = [
+        ("req", lc_req),
+        ("key_flags", C.c_uint32),
+        ("k", C.c_uint32 * 3),
+        ("lam", C.c_double * 3),
     ]
 
 
@@ -114,6 +128,22 @@ class lc_byte_stats_t(C.Structure):
     ]
 
 
+class lc_digit_stats_t(C.Structure):
+    _fields_ = [
+        ("states", C.c_uint64),
+        ("int_part", (C.c_uint64 * 128) * 3),
+        ("digits", ((C.c_uint64 * 100) * 3) * 3),
+        ("out_of_range", C.c_uint64 * 3),
+    ]
+
+    def arrays(self):
+        """(int_part [3, 128], digits [3, 3, 100], out_of_range [3]) as numpy."""
+        import numpy as np
+        ip = np.array([list(self.int_part[c]) for c in range(3)], dtype=np.uint64)
+        dg = np.array([[list(self.digits[c][j]) for j in range(3)] for c in range(3)], dtype=np.uint64)
+        return ip, dg, np.array(list(self.out_of_range), dtype=np.uint64)
+
+
 class LcError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -170,6 +200,12 @@ _SIGNATURES = {
     "lc_byte_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32,
                                 C.POINTER(lc_byte_stats_t), C.c_void_p]),
     "lc_synth_uniform": (C.c_int, [C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint64, C.c_void_p]),
+    "lc_ctx_digit_stats": (C.c_int, [C.c_void_p, C.c_int]),
+    "lc_run_batch_ex": (C.c_int, [C.c_void_p, C.POINTER(lc_req_ex), C.c_size_t, C.c_void_p, C.c_int,
+                                  C.c_void_p]),
+    "lc_plan_batch_ex": (C.c_int, [C.POINTER(lc_params), C.POINTER(lc_req_ex), C.c_size_t, C.c_int,
+                                   C.c_void_p, C.POINTER(C.c_uint64)]),
+    "lc_ctx_get_digit_stats": (C.c_int, [C.c_void_p, C.POINTER(lc_digit_stats_t)]),
 }
 
 
@@ -366,6 +402,49 @@ class Batch:
             r.out_cap = out_cap
 
 
+class BatchEx:
+    """An lc_req_ex array (requests with their own key material) plus the
+    password buffers it points to."""
+
+    def __init__(self, items):
+        """items: iterable of (pw, dir, in, in_len, out, out_cap, lam, k), where
+        lam and k are 3-sequences or None (the context's value)."""
+        items = list(items)
+        self._pw = []
+        self.reqs = (lc_req_ex * max(1, len(items)))()
+        self.count = len(items)
+        for i, (pw, d, inp, in_len, out, out_cap, lam, k) in enumerate(items):
+            buf, L = _pwbuf(pw)
+            self._pw.append(buf)
+            e = self.reqs[i]
+            r = e.req
+            r.pw = C.cast(buf, C.c_void_p)
+            r.pw_len = L
+            r.dir = d
+            r.inp = _ptr(inp)
+            r.in_len = in_len
+            r.out = _ptr(out)
+            r.out_cap = out_cap
+            e.key_flags = (LC_KEY_LAMBDA if lam is not None else 0) | (LC_KEY_K if k is not None else 0)
+            for j in range(3):
+                e.lam[j] = lam[j] if lam is not None else 0.0
+                e.k[j] = k[j] if k is not None else 0
+
+
+def lc_run_batch_ex(ctx, batch: BatchEx, status_dev, mode=LC_PARALLEL, stream=None) -> int:
+    return load().lc_run_batch_ex(ctx, batch.reqs, batch.count, _ptr(status_dev), mode, _stream(stream))
+
+
+def lc_plan_batch_ex(batch: BatchEx, mode=LC_PARALLEL, p: lc_params = None):
+    """(status, per-request init statuses, parts) of a host-only validation."""
+    import numpy as np
+    st = np.zeros(max(1, batch.count), dtype=np.int32)
+    rows = C.c_uint64(0)
+    rc = load().lc_plan_batch_ex(C.byref(p) if p is not None else None, batch.reqs, batch.count, mode,
+                                 st.ctypes.data, C.byref(rows))
+    return rc, st[:batch.count], rows.value
+
+
 def lc_run_batch(ctx, batch: Batch, status_dev, mode=LC_PARALLEL, stream=None) -> int:
     return load().lc_run_batch(ctx, batch.reqs, batch.count, _ptr(status_dev), mode, _stream(stream))
 
@@ -501,6 +580,16 @@ def autocorrelation(stats: lc_byte_stats_t, max_lag=LC_STATS_MAX_LAG):
         m = n - k
         cov = stats.lag_sum[k - 1] / m - mean * mean if m > 0 else 0.0
         out.append(cov / var if var > 0 else 0.0)
+    return out
+
+
+def lc_ctx_digit_stats(ctx, enable: bool) -> int:
+    return load().lc_ctx_digit_stats(ctx, 1 if enable else 0)
+
+
+def lc_ctx_get_digit_stats(ctx) -> lc_digit_stats_t:
+    out = lc_digit_stats_t()
+    check(load().lc_ctx_get_digit_stats(ctx, C.byref(out)), "lc_ctx_get_digit_stats")
     return out
 
 

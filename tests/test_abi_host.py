@@ -39,7 +39,8 @@ def test_version_and_status_strings():
 def test_default_params_match_oracle_v1():
     p = lc.lc_params_default()
     q = O.params()
-    for f in ("sigma", "rho", "beta", "dt", "n_warm", "steps_per_byte", "block_len", "tag_len", "eta"):
+    for f in ("sigma", "rho", "beta", "dt", "n_warm", "steps_per_byte", "block_len", "tag_len", "eta",
+              "omega_alpha_shift", "reserved"):
         assert getattr(p, f) == getattr(q, f), f
     assert list(p.lam) == list(q.lam) and list(p.k) == list(q.k)
 
@@ -123,6 +124,33 @@ def test_batch_validation():
     rc, st, rows = lc.lc_plan_batch(b, lc.LC_PARALLEL)
     assert rc == lc.LC_OK
     assert list(st) == [want for _, want in cases]
+
+
+def test_per_request_key_material_validation():
+    # Sec. 3.1: -15.67 < lambda_1 < 16.01, -11.28 < lambda_2 < 16.01,
+    # 0.090 < lambda_3 < 62, 2 < k_i <= 4; outside them the request fails.
+    A = 0x1000_0000
+    base = (b"pw", 0, A, 100, A + 4096, 108)
+    cases = [
+        (None, None, lc.LC_OK),
+        ((1.0, 1.0, 20.0), (4, 4, 4), lc.LC_OK),
+        ((-15.66, -11.27, 0.091), (3, 3, 3), lc.LC_OK),
+        ((16.0, 16.0, 61.99), None, lc.LC_OK),
+        (None, (3, 4, 3), lc.LC_OK),
+        ((-15.67, 0.0, 20.0), None, lc.LC_ERR_ARG),
+        ((0.0, 16.01, 20.0), None, lc.LC_ERR_ARG),
+        ((0.0, 0.0, 0.09), None, lc.LC_ERR_ARG),
+        ((0.0, 0.0, 62.0), None, lc.LC_ERR_ARG),
+        ((float("nan"), 0.0, 20.0), None, lc.LC_ERR_ARG),
+        (None, (2, 4, 4), lc.LC_ERR_ARG),
+        (None, (4, 5, 4), lc.LC_ERR_ARG),
+        (None, (4, 4, 0), lc.LC_ERR_ARG),
+    ]
+    b = lc.BatchEx([base + (lam, k) for lam, k, _ in cases] + [(b"", 0, A, 100, A + 4096, 108, None, (3, 3, 3))])
+    rc, st, rows = lc.lc_plan_batch_ex(b, lc.LC_PARALLEL)
+    assert rc == lc.LC_OK
+    assert list(st) == [want for _, _, want in cases] + [lc.LC_ERR_PASSWORD]
+    assert rows == sum(1 for _, _, w in cases if w == lc.LC_OK)
 
 
 def test_context_needs_a_gpu():

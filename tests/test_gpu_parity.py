@@ -230,6 +230,8 @@ PROFILES = [
     dict(block_len=64, tag_len=3),
     dict(lam=(-15.0, -11.0, 61.0), eta=2.0 ** -10),
     dict(sigma=0.0, rho=0.0, beta=0.0, dt=0.0, lam=(1.5, 1.5, 1.5)),
+    dict(omega_alpha_shift=1),           # Step 3's alpha index read with 0-based i
+    dict(omega_alpha_shift=1, k=(3, 4, 3)),
 ]
 
 
@@ -676,9 +678,9 @@ def test_one_context_two_streams(ctx):
 
 def test_message_over_4gib(ctx):
     # One message just over 2^32 bytes: part offsets b * 4096 and tag offsets
-    # n + 8 b pass 2^32.  Every byte of the 16,384 parts around the boundary,
-    # the first two parts and the last two (the ragged one) equal the oracle;
-    # the whole message round-trips.
+    # n + 8 b pass 2^32.  Every byte of the last 16,384 parts (across the
+    # boundary, up to the ragged last one) and of the first two parts equals
+    # the oracle; the whole message round-trips.
     n = (1 << 32) + 3 * B + 5
     seed = 0x4_0000_0001
     pw = b"over-four-gibibytes"
@@ -697,10 +699,12 @@ def test_message_over_4gib(ctx):
         O.encrypt_blocks(key, Ph, n, Cb, b, b + 1)
         assert np.array_equal(host(Cd[lo:hi]), Cb[lo:hi]), b
         assert np.array_equal(host(Cd[n + T * b:n + T * b + T]), Cb[n + T * b:n + T * b + T]), b
-    # every byte of the 64 MiB around the 2^32 boundary (16,384 parts) and
+    # every byte of the last 16,384 parts (the 64 MiB that end the message:
+    # parts on both sides of the 2^32 boundary and the ragged last one) and
     # of their tags, the oracle on all cores
-    b0, b1 = edge - 8192, edge + 8192
-    lo, hi = b0 * B, b1 * B
+    b0, b1 = nb - 16384, nb
+    assert b0 < edge < b1
+    lo, hi = b0 * B, n
     Ph[lo:hi] = oracle_mt.uniform(seed, hi - lo, lo)
     jobs = [(c, min(b1, c + 64)) for c in range(b0, b1, 64)]
     from concurrent.futures import ThreadPoolExecutor
@@ -714,3 +718,52 @@ def test_message_over_4gib(ctx):
     step = 1 << 30
     for a in range(0, n, step):
         assert torch.equal(back[a:a + step], P[a:a + step]), a
+
+
+# ---------------------------------------------------------------------------
+# per-request key material: lambda (Eq. 5) and k (Eq. 7)
+# ---------------------------------------------------------------------------
+
+KEYS = [
+    (None, None),                                   # the context's (1, 1, 20), (4, 4, 4)
+    ((-15.0, -11.0, 61.0), (3, 4, 3)),
+    ((15.9, 15.9, 0.1), (3, 3, 3)),
+    ((0.5, -2.25, 30.0), None),                     # lambda only: the v1 variant
+    (None, (4, 3, 4)),
+]
+
+
+@pytest.mark.parametrize("mode", [lc.LC_PARALLEL, lc.LC_SEQUENTIAL])
+@pytest.mark.parametrize("k_in_batch", [True, False], ids=["mixed-k", "lambda-only"])
+def test_per_request_lambda_and_k(ctx, mode, k_in_batch):
+    # One batch mixes requests with their own (lambda, k) and with the
+    # context's; each equals the oracle run with those parameters, in both
+    # directions.  Without a k != 4 in the batch the v1 kernel variant runs.
+    keys = KEYS if k_in_batch else [kk for kk in KEYS if kk[1] is None]
+    items, expect, keep = [], [], []
+    for i, n in enumerate([0, 1, 33, B, B + 1, 3 * B + 7, 20000, 70001]):
+        for j, (lam, k) in enumerate(keys):
+            pw = synth.password(synth.subseed(90, 10 * i + j), 4 + (3 * i + j) % 29)
+            P = synth.uniform_bytes(synth.subseed(91, 10 * i + j), n)
+            po = O.params(**({"lam": lam} if lam else {}), **({"k": k} if k else {}))
+            ct = O.encrypt(pw, P, mode, po)
+            d = (i + j) % 2
+            src, want = (P, ct) if d == 0 else (ct, P)
+            x = dev(src) if src.size else torch.zeros(1, dtype=torch.uint8, device="cuda")
+            y = torch.full((max(1, want.size),), 0x3C, dtype=torch.uint8, device="cuda")
+            keep += [x, y]
+            items.append((pw, d, x if src.size else None, src.size, y, want.size, lam, k))
+            expect.append(want)
+    st = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+    lc.check(lc.lc_run_batch_ex(ctx.handle, lc.BatchEx(items), st, mode))
+    assert (host(st) == 0).all()
+    for it, want in zip(items, expect):
+        assert np.array_equal(host(it[4])[:want.size], want), it[:2] + it[6:]
+    # a wrong k is a wrong key: the decryption is rejected and zeroed
+    pw, P = b"wrong-k", synth.uniform_bytes(92, 5000)
+    ct = O.encrypt(pw, P, mode, O.params(k=(3, 3, 3)))
+    x, y = dev(ct), torch.ones(P.size, dtype=torch.uint8, device="cuda")
+    s1 = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    lc.check(lc.lc_run_batch_ex(ctx.handle, lc.BatchEx([(pw, 1, x, ct.size, y, P.size, None, (4, 3, 3))]),
+                                s1, mode))
+    assert host(s1)[0] == lc.LC_ERR_INTEGRITY and not host(y).any()

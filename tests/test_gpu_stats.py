@@ -67,3 +67,65 @@ def test_ciphertext_statistics(ctx):
     lc.check(lc.lc_synth_uniform(U, n, 62, 0))
     cu = lc.lc_byte_stats(ctx.handle, ctx.encrypt(b"uniform", U), n)
     assert lc.entropy_bits(cu) > 7.999
+
+
+# ---------------------------------------------------------------------------
+# Fig. 1: digit statistics of the trajectory coordinates
+# ---------------------------------------------------------------------------
+
+def _oracle_digits(msgs, prm):
+    """The oracle's Fig. 1 counts over the encryption of (pw, P) messages in
+    parallel mode."""
+    import oracle as O
+    st = O.Stats()
+    for pw, P in msgs:
+        key = O.key_schedule(pw, prm)
+        n = P.size
+        Cb = np.zeros(O.ciphertext_len(n, prm=prm), np.uint8)
+        O.encrypt_blocks(key, np.ascontiguousarray(P), n, Cb, 0, O.nblocks(n, prm=prm), prm, st)
+    return st.digit_arrays(), int(st.steps)
+
+
+@pytest.mark.parametrize("over", [{}, {"dt": 0.027}, {"k": (3, 4, 4), "steps_per_byte": 2}],
+                         ids=["v1", "dt0.027", "general"])
+def test_fig1_digit_stats_match_oracle(over):
+    # Every count of the counting kernels equals the oracle's over the same
+    # encryptions; decrypting the ciphertexts follows the same trajectories,
+    # so it doubles every count.  The outputs are unchanged by counting.
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    prm = O.params(**over)
+    sizes = [1, 100, 4096, 4097, 3 * 4096 + 77, 70000]
+    msgs = [(synth.password(synth.subseed(80, i), 5 + i), synth.uniform_bytes(synth.subseed(81, i), n))
+            for i, n in enumerate(sizes)]
+    (want_ip, want_dg, want_oor), steps = _oracle_digits(msgs, prm)
+    with lc.Context(0, lc.params(**over)) as c:
+        ins = [torch.from_numpy(P).cuda() for _, P in msgs]
+        outs = [torch.zeros(c.ciphertext_len(P.size), dtype=torch.uint8, device="cuda") for _, P in msgs]
+        items = [(pw, 0, x, x.numel(), y, y.numel()) for (pw, _), x, y in zip(msgs, ins, outs)]
+        st = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+        lc.check(lc.lc_ctx_digit_stats(c.handle, True))
+        lc.check(lc.lc_run_batch(c.handle, lc.Batch(items), st))
+        d = lc.lc_ctx_get_digit_stats(c.handle)
+        assert (st.cpu().numpy() == 0).all()
+        ip, dg, oor = d.arrays()
+        assert d.states == steps
+        assert np.array_equal(ip, want_ip) and np.array_equal(dg, want_dg)
+        assert np.array_equal(oor, want_oor)
+        for (pw, P), y in zip(msgs, outs):
+            assert np.array_equal(y.cpu().numpy(), O.encrypt(pw, P, O.PARALLEL, prm))
+        # decrypting (still counting) adds the same counts again
+        backs = [torch.zeros(max(1, P.size), dtype=torch.uint8, device="cuda") for _, P in msgs]
+        items = [(pw, 1, y, y.numel(), b, P.size) for (pw, P), y, b in zip(msgs, outs, backs)]
+        lc.check(lc.lc_run_batch(c.handle, lc.Batch(items), st))
+        ip2, dg2, oor2 = lc.lc_ctx_get_digit_stats(c.handle).arrays()
+        assert (st.cpu().numpy() == 0).all()
+        assert np.array_equal(ip2, 2 * want_ip) and np.array_equal(dg2, 2 * want_dg)
+        assert np.array_equal(oor2, 2 * want_oor)
+        # counting off: the counters stay, the kernels go back to the fast build
+        lc.check(lc.lc_ctx_digit_stats(c.handle, False))
+        lc.check(lc.lc_run_batch(c.handle, lc.Batch(items), st))
+        assert np.array_equal(lc.lc_ctx_get_digit_stats(c.handle).arrays()[0], 2 * want_ip)
+        if over.get("dt") == 0.027:
+            assert int(want_oor.sum()) > 0  # the divergent profile reaches |v| >= 2^31

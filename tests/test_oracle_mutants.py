@@ -30,7 +30,8 @@ MU = ("  for (i = 0; i < 3; i++)\n"
       "    st->mu[i] = (st->mu[i] + lco_rbyte(st->alpha[i], st->omega[i])) % 3u;\n")
 ALPHA = "  for (i = 0; i < 3; i++) st->alpha[i] = st->r[st->mu[i]];\n"
 OMEGA = ("  for (i = 0; i < 3; i++)\n"
-         "    st->omega[i] = (st->omega[i] + lco_rbyte(st->alpha[i], st->omega[i])) % p->k[i];\n")
+         "    st->omega[i] = (st->omega[i] + lco_rbyte(st->alpha[p->omega_alpha_shift ? (i + 2) % 3 : i],\n"
+         "                                             st->omega[i])) % p->k[i];\n")
 APRIME = "  for (i = 0; i < 3; i++) st->r[i] = st->r[i] + K->aprime[i];\n"
 WARM = "  for (s = 0; s < p->n_warm; s++) lco_euler_step(p, st->r);\n"
 START_COPY = ("  for (j = 0; j < 3; j++) {\n    st->mu[j] = K->mu[j];\n"

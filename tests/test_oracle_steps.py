@@ -258,3 +258,130 @@ def test_trajectory_start_point():
         st = O.block_begin(key(aprime=ap), b, p)
         for j in range(3):
             assert st.r[j] == (ap[j] + p.lam[j]) + b * 2.0 ** -24, (b, j)
+
+
+# --------------------------------------------------------------------------
+# Fig. 1 (Sec. 3.1): digit statistics of the trajectory coordinates
+# --------------------------------------------------------------------------
+
+def _decimal_counts(vals):
+    """Expected Fig. 1 counts of coordinate values from their exact decimal
+    expansion: trunc(v) + 64 (clamped), floor(|v| 10^(2j+2)) mod 100 for the
+    digit pairs 1-2, 3-4, 5-6; |v| >= 2^31 or NaN out of range.  Returns the
+    counts and whether a value's scaled magnitude lies within one rounding
+    error (|t| 2^-52) below an integer, where the binary64 product may reach it."""
+    from decimal import Decimal, ROUND_DOWN, ROUND_FLOOR
+    ip = np.zeros((3, 128), np.uint64)
+    dg = np.zeros((3, 3, 100), np.uint64)
+    oor = np.zeros(3, np.uint64)
+    near = False
+    for c, v in vals:
+        if not (abs(v) < 2.0 ** 31):
+            oor[c] += 1
+            continue
+        d = Decimal(v)  # exact binary value
+        ip[c][min(127, max(0, int(d.to_integral_value(ROUND_DOWN)) + 64))] += 1
+        a = abs(d)
+        for j in range(3):
+            t = a * (Decimal(10) ** (2 * j + 2))
+            f = t.to_integral_value(ROUND_FLOOR)
+            # rounding the product to nearest can only lift it to the next
+            # integer when it lies just below one
+            if (f + 1 - t) <= t * Decimal(2) ** -52:
+                near = True
+            dg[c][j][int(f) % 100] += 1
+    return ip, dg, oor, near
+
+
+def test_fig1_digit_counts_follow_the_decimal_expansion():
+    # Frozen dynamics (F = identity) and a zero byte (no kick): the state the
+    # oracle counts after the Euler step is exactly the state set by hand.
+    p = O.params(sigma=0.0, rho=0.0, beta=0.0, dt=0.0)
+    rng = np.random.default_rng(77)
+    cases = [(-0.0, 12.3456789, 63.99), (-64.5, 127.25, -1e-7), (float("nan"), 2.0 ** 31, -2.0 ** 31),
+             (0.005, 0.995, 99.999999), (-17.000001, 1e9, -3.5)]
+    cases += [tuple(float(v) for v in rng.uniform(-70, 70, 3)) for _ in range(300)]
+    cases += [tuple(float(v) for v in rng.standard_normal(3) * 10 ** rng.uniform(-4, 9, 3))
+              for _ in range(300)]
+    stats = O.Stats()
+    vals, skipped = [], 0
+    for r in cases:
+        want = _decimal_counts([(c, r[c]) for c in range(3)])
+        if want[3]:
+            skipped += 1  # within one rounding of a digit boundary
+            continue
+        st = state(r, (0.0, 0.0, 0.0), (0, 1, 2), (0, 0, 0))
+        O.step_byte(key(), st, 0, O.ENCRYPT, p, stats)
+        vals += [(c, r[c]) for c in range(3)]
+    assert skipped < 20 and len(vals) >= 3 * 580
+    ip, dg, oor = stats.digit_arrays()
+    want_ip, want_dg, want_oor, _ = _decimal_counts(vals)
+    assert np.array_equal(ip, want_ip)
+    assert np.array_equal(dg, want_dg)
+    assert np.array_equal(oor, want_oor)
+    assert int(stats.steps) == len(vals) // 3
+
+
+def test_fig1_shape_on_a_v1_trajectory():
+    # Fig. 1: the integer parts of the coordinates stay in a short range and
+    # the digit pairs 3-4 and 5-6 are close to uniform.
+    import scipy.stats as ss
+    from paper_1201_3114_gb300 import synth
+    prm = O.params()
+    key_ = O.key_schedule("123456", prm)
+    n = 1 << 19
+    P = synth.uniform_bytes(3, n)
+    Cb = np.zeros(O.ciphertext_len(n, prm=prm), np.uint8)
+    st = O.Stats()
+    O.encrypt_blocks(key_, P, n, Cb, 0, O.nblocks(n, prm=prm), prm, st)
+    ip, dg, oor = st.digit_arrays()
+    assert int(oor.sum()) == 0
+    for c in range(3):
+        used = np.flatnonzero(ip[c])
+        assert used.size and used.max() - used.min() < 64, c  # |v| stays below ~50
+        assert int(ip[c].sum()) == int(st.steps)
+        for j in (1, 2):
+            assert ss.chisquare(dg[c][j].astype(float)).pvalue > 1e-4, (c, j)
+
+
+def test_step3_cyclic_alpha_index_profile(prm):
+    # The other reading of Step 3's alpha index [(i+2) mod 3]+1: with 0-based
+    # i (omega_alpha_shift = 1) Omega_1 moves with alpha_3, Omega_2 with
+    # alpha_1 and Omega_3 with alpha_2 (the new alphas, the old Omegas).
+    p = O.params(omega_alpha_shift=1)
+    n_diff = 0
+    for c in _step3_cases(prm, 60):
+        st = state((0.0, 0.0, c["z0"]), c["alpha"], c["mu"], c["om"])
+        O.step_byte(key(aprime=c["ap"]), st, c["x"], O.ENCRYPT, p)
+        om = c["om"]
+        a = [st.alpha[i] for i in range(3)]
+        want = tuple((om[i] + rb(a[(i + 2) % 3], om[i])) % 4 for i in range(3))
+        ident = tuple((om[i] + rb(a[i], om[i])) % 4 for i in range(3))
+        assert tuple(st.omega) == want
+        n_diff += want != ident
+        assert tuple(st.mu) == c["mu_new"]  # mu and alpha as in the default reading
+    assert n_diff >= 20
+
+
+def test_both_alpha_index_readings_lock():
+    # The cyclic reading does not avoid the (mu, Omega) lock: once all three
+    # components share mu and Omega, their alphas coincide and every update
+    # rule that treats the components alike keeps them equal, whatever the
+    # alpha index.  Under both readings every part of a v1 run reaches that
+    # triple lock within a few dozen bytes, after which C - P = 2 R is even.
+    P = np.zeros(4096, np.uint8)
+    for shift in (0, 1):
+        prm = O.params(omega_alpha_shift=shift)
+        key_ = O.key_schedule("123456", prm)
+        st = O.block_begin(key_, 0, prm)
+        locked_at = None
+        for i in range(400):
+            O.step_byte(key_, st, 0, O.ENCRYPT, prm)
+            triple = len(set(st.mu)) == 1 and len(set(st.omega)) == 1
+            if locked_at is None and triple:
+                locked_at = i
+            if locked_at is not None:
+                assert triple, (shift, i)  # absorbing
+        assert locked_at is not None and locked_at < 100, (shift, locked_at)
+        c = O.encrypt("123456", P, O.PARALLEL, prm)[:4096].astype(int)
+        assert np.all((c[128:] - P[128:].astype(int)) % 2 == 0), shift
