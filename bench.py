@@ -205,9 +205,11 @@ def measured_peaks():
         return {}
 
 
-def committed_traffic():
-    """DRAM traffic per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def committed_traffic(dense_build=0):
+    """DRAM bytes and warp instructions per message byte of the throughput
+    variant's build (the default one, or the dense one when dense_build) from
+    the committed ncu summary, if it was taken on the current kernel
+    sources."""
     path = os.path.join(ROOT, "profiles", "batch_kernel_traffic.json")
     try:
         with open(path) as f:
@@ -216,7 +218,7 @@ def committed_traffic():
         return None
     if rec.get("source_hash") != source_hash():
         return None
-    return rec
+    return rec.get("builds", {}).get("dense" if dense_build else "default")
 
 
 # ---------------------------------------------------------------------------
@@ -361,6 +363,55 @@ def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_
     return out, sample
 
 
+def oracle_config_rates(threads, cfg3_mib=256):
+    """The oracle timed on the single-message configurations: 64 KiB and the
+    1 MiB text (parallel mode on one core and on all cores, sequential mode on
+    one core: it is one trajectory), and a sample of the 1 GiB message (its
+    first cfg3_mib MiB, all cores).  Message bytes per second, decimal GB."""
+    import oracle as O
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1201_3114_gb300 import synth
+    prm = O.params()
+
+    def par(pw, P, nthreads):
+        key = O.key_schedule(pw, prm)
+        n = P.size
+        nb = max(1, -(-n // 4096))
+        Cb = np.zeros(O.ciphertext_len(n, O.PARALLEL, prm), dtype=np.uint8)
+        step = max(1, min(64, -(-nb // nthreads)))
+        jobs = [(b, min(nb, b + step)) for b in range(0, nb, step)]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(nthreads) as ex:
+            list(ex.map(lambda j: O.encrypt_blocks(key, P, n, Cb, j[0], j[1], prm), jobs))
+        return n / (time.perf_counter() - t0) / 1e9
+
+    out = {}
+    c1 = synth.cfg1()
+    out["cfg1_64k"] = {"one_core_GBps": par(c1["pw"], c1["P"], 1),
+                       "all_cores_GBps": par(c1["pw"], c1["P"], threads)}
+    c2 = synth.cfg2()
+    t0 = time.perf_counter()
+    O.encrypt(c2["pw"], c2["P"], O.SEQUENTIAL, prm)
+    seq = c2["P"].size / (time.perf_counter() - t0) / 1e9
+    out["cfg2_1mib"] = {"parallel_one_core_GBps": par(c2["pw"], c2["P"], 1),
+                        "parallel_all_cores_GBps": par(c2["pw"], c2["P"], threads),
+                        "sequential_one_core_GBps": seq}
+    spec = synth.cfg3_spec()
+    n3 = cfg3_mib << 20
+    P3 = np.empty(n3, dtype=np.uint8)
+    chunk = 16 << 20
+
+    def fill(a):
+        P3[a:a + chunk] = synth.uniform_bytes(spec["data_seed"], min(chunk, n3 - a), a)
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(fill, range(0, n3, chunk)))
+    out["cfg3_1gib"] = {"all_cores_GBps": par(spec["pw"], P3, threads),
+                        "sample": "the first %d MiB of the 1 GiB message" % cfg3_mib}
+    out["cores"] = threads
+    return out
+
+
 def oracle_check_served(sample, threads):
     """CPU-baseline leg for the served configuration: the oracle encrypts the
     captured sample (plaintexts regenerated on the host from the pool's
@@ -494,7 +545,7 @@ def single_message_configs(ctx, dev, stream, pipes, sm_mhz, reps=20):
     del back
     sizes = [n3]
     ops, parts, _ = fp64_ops_per_launch(sizes)
-    rl = roofline_terms(sizes, kms, pipes, sm_mhz)
+    rl = roofline_terms(sizes, kms, pipes, sm_mhz, dense_build=lc.lc_ctx_get_launch(ctx.handle).dense_build)
     out["cfg3_1gib"] = {"bytes": n3, "parts": parts, "ms_per_encrypt": ms, "GBps": n3 / ms / 1e6,
                         "kernel_ms": kms, "kernel_GBps": n3 / kms / 1e6,
                         "fp64_ops_per_launch": ops, "fp64_gops": ops / (kms * 1e-3) / 1e9,
@@ -507,7 +558,7 @@ def single_message_configs(ctx, dev, stream, pipes, sm_mhz, reps=20):
     return out
 
 
-def roofline_terms(sizes, kernel_ms, pipes, sm_mhz, n_warm=3000, steps=1, B=4096, T=8):
+def roofline_terms(sizes, kernel_ms, pipes, sm_mhz, n_warm=3000, steps=1, B=4096, T=8, dense_build=0):
     """Roofline figures of one cipher-kernel launch over messages of these
     sizes:
       method_roofline_GBps  the bound the method statement names: the slower of
@@ -530,7 +581,7 @@ def roofline_terms(sizes, kernel_ms, pipes, sm_mhz, n_warm=3000, steps=1, B=4096
     mask = lc.lc_emu_mask()
     hw_ops = fp64_pipe_ops_per_launch(sizes, mask, n_warm, steps, B, T)
     t_fp64 = hw_ops / (pipes.dadd_gops * 1e9) * 1e3
-    rec = committed_traffic()
+    rec = committed_traffic(dense_build)
     joint = None
     if rec and rec.get("inst_executed_per_message_byte") and sm_mhz:
         inst = rec["inst_executed_per_message_byte"] * msg_bytes
@@ -541,8 +592,9 @@ def roofline_terms(sizes, kernel_ms, pipes, sm_mhz, n_warm=3000, steps=1, B=4096
                  "frac": bound / kernel_ms,
                  "fp64_pipe_ops": hw_ops, "fp64_pipe_rate_gops": pipes.dadd_gops,
                  "warp_instructions": inst, "sm_count": pipes.sm_count, "sm_mhz": sm_mhz,
+                 "build": "dense" if dense_build else "default",
                  "note": "warp instructions scaled from the committed ncu count per message byte "
-                         "(profiles/batch_kernel_traffic.json, same kernel sources)"}
+                         "of the same build (profiles/batch_kernel_traffic.json, same kernel sources)"}
     return {"method_roofline_GBps": method_gbps,
             "fp64_pipe_frac_of_probe": (hw_ops / (kernel_ms * 1e-3) / 1e9) / pipes.dadd_gops,
             "joint": joint}
@@ -560,6 +612,12 @@ def profile_case(args):
     lc.check(lc.lc_synth_uniform(P, n, 0x1201311400CA5E, 0, stream))
     Cb = torch.empty(ctx.ciphertext_len(n), dtype=torch.uint8, device="cuda")
     pw = b"profile-case-24-chars-pw"
+    if args.profile_launch:
+        tpc, dense = (int(v) for v in args.profile_launch.split(","))
+        l = lc.lc_ctx_get_launch(ctx.handle)
+        l.threads_per_cta, l.dense_build = tpc, dense
+        lc.check(lc.lc_ctx_set_launch(ctx.handle, l.threads_per_cta, l.ctas_per_sm, l.smem_staging,
+                                      l.small_batch_rows, l.host_chunk_mib, l.dense_build))
     for _ in range(args.warmup):
         lc.check(lc.lc_encrypt(ctx.handle, pw, P, n, Cb, Cb.numel(), lc.LC_PARALLEL, stream))
     lc.check(lc.lc_ctx_timing(ctx.handle, True))
@@ -581,10 +639,18 @@ def profile_case(args):
     s1.record(stream)
     torch.cuda.synchronize()
     stats_ms = s0.elapsed_time(s1)
+    # and one histogram-only pass (the direct kernel)
+    s0.record(stream)
+    lc.lc_byte_stats(ctx.handle, Cb, n, 0, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    hist_ms = s0.elapsed_time(s1)
     print(json.dumps({"case": "profile", "mib": args.profile_case, "ms_per_step": ms,
                       "GBps": n / ms / 1e6, "kernel_ms": kms / max(1, kn),
                       "fp64_gops": ops / (kms / max(1, kn)) / 1e6, "source_hash": source_hash(),
                       "stats_ms": stats_ms, "stats_GBps": n / stats_ms / 1e6,
+                      "histogram_ms": hist_ms, "histogram_GBps": n / hist_ms / 1e6,
+                      "launch": lc.lc_ctx_get_launch(ctx.handle).as_dict(),
                       "ciphertext_entropy_bits": lc.entropy_bits(st)}))
     ctx.close()
     return 0
@@ -675,10 +741,36 @@ def next_rows(args):
         n = 1 << 30
         P = torch.empty(n, dtype=torch.uint8, device="cuda")
         lc.check(lc.lc_synth_uniform(P, n, synth.config_seed(3) + 20, 0, stream))
-        ms = timed(lambda: lc.lc_byte_stats(ctx.handle, P, n, 8, stream), args.steps)
         peak = measured_peaks().get("hbm_gbs")
-        out["stats_1GiB"] = {"ms": ms, "GBps": n / ms / 1e6, "hbm_peak_GBps": peak,
-                             "frac_of_measured_hbm": (n / ms / 1e6) / peak if peak else None}
+        for lags, key in ((8, "stats_1GiB"), (0, "stats_1GiB_histogram_only")):
+            ms = timed(lambda: lc.lc_byte_stats(ctx.handle, P, n, lags, stream), args.steps)
+            out[key] = {"max_lag": lags, "ms": ms, "GBps": n / ms / 1e6, "hbm_peak_GBps": peak,
+                        "frac_of_measured_hbm": (n / ms / 1e6) / peak if peak else None,
+                        "note": "synchronous call: memset, kernel, read-back of the counters"}
+
+        # the same statistics fused into the cipher kernel: a 1 GiB
+        # encryption with counting on, against the plain encryption followed
+        # by the separate pass over its ciphertext
+        Cb = torch.empty(ctx.ciphertext_len(n), dtype=torch.uint8, device="cuda")
+        pw = b"fused-statistics-24chars"
+        enc = lambda: lc.check(lc.lc_encrypt(ctx.handle, pw, P, n, Cb, Cb.numel(), lc.LC_PARALLEL, stream))
+        ms_plain = timed(enc, args.steps)
+        ms_pass = timed(lambda: lc.lc_byte_stats(ctx.handle, Cb, Cb.numel(), 8, stream), args.steps)
+        lc.check(lc.lc_ctx_ciphertext_stats(ctx.handle, True))
+        ms_fused = timed(enc, args.steps)
+        fused = lc.lc_ctx_get_ciphertext_stats(ctx.handle)
+        lc.check(lc.lc_ctx_ciphertext_stats(ctx.handle, False))
+        sep = lc.lc_byte_stats(ctx.handle, Cb, Cb.numel(), 8, stream)
+        reps = args.warmup + args.steps
+        same = (fused.n == reps * sep.n and list(fused.hist) == [reps * h for h in sep.hist]
+                and list(fused.lag_sum) == [reps * v for v in sep.lag_sum])
+        if not same:
+            raise SystemExit("fused ciphertext statistics differ from the separate pass")
+        out["stats_fused_1GiB"] = {
+            "encrypt_ms": ms_plain, "encrypt_counting_ms": ms_fused, "separate_pass_ms": ms_pass,
+            "fused_overhead_ms": ms_fused - ms_plain,
+            "fused_overhead_frac": (ms_fused - ms_plain) / ms_plain,
+            "separate_pass_frac": ms_pass / ms_plain, "equal_to_separate_pass": same}
     print(json.dumps(out))
     return 0
 
@@ -709,6 +801,9 @@ def main():
     ap.add_argument("--serve-policy", default="small_first", choices=["small_first", "fifo"],
                     help="order in which waiting requests fill a batch")
     ap.add_argument("--serve-batch-mib", type=int, default=256, help="bytes per served batch (cap)")
+    ap.add_argument("--profile-launch", default="", metavar="THREADS,DENSE",
+                    help="--profile-case: threads per CTA and dense build of the cipher kernel "
+                         "(default: the context's default launch shape)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="MIB",
                     help="only time one MIB-MiB parallel-mode encryption per step (a small "
                          "case for ncu captures); prints a short JSON line")
@@ -829,13 +924,14 @@ def main():
     achieved = ops / (kern_avg_ms * 1e-3) / 1e9  # G FP64 ops / s
     pipes = lc.lc_probe_pipes(local)
     peak = NOMINAL_FP64_TFLOPS * 1e3 / 2.0
-    traffic = committed_traffic()
+    traffic = committed_traffic(launch.dense_build)
     mask = lc.lc_emu_mask()
     hw_ops = fp64_pipe_ops_per_launch(sizes, mask, prm.n_warm, prm.steps_per_byte,
                                       prm.block_len, prm.tag_len)
     hw_rate = hw_ops / (kern_avg_ms * 1e-3) / 1e9
     rl_terms = roofline_terms(sizes, kern_avg_ms, pipes, clk.get("sm_mhz") or pipes.sm_clock_mhz,
-                              prm.n_warm, prm.steps_per_byte, prm.block_len, prm.tag_len)
+                              prm.n_warm, prm.steps_per_byte, prm.block_len, prm.tag_len,
+                              launch.dense_build)
     roofline = {
         "bound": "alu", "unit": "G FP64 op/s", "achieved": achieved, "peak": peak,
         "frac": achieved / peak,
@@ -847,7 +943,9 @@ def main():
                        "(no FP64 entry in the measured peaks)",
         "peak_probe": pipes.dadd_gops, "frac_of_probe": achieved / pipes.dadd_gops,
         "ops_per_launch": ops, "kernel_ms": kern_avg_ms, "kernel": "batch_kernel",
-        "traffic": traffic["bytes_per_launch"] if traffic else None,
+        "traffic": traffic["dram_bytes_per_message_byte"] * msg_bytes if traffic else None,
+        "traffic_source": ("ncu capture of the same build on one %s, scaled by message bytes"
+                           % traffic["captured_case"]) if traffic else None,
         "hbm_bytes_algorithmic": 2 * msg_bytes + 8 * parts,
         "note": "achieved counts every binary64 operation of the path; the kernel runs the "
                 "ones in emu_mask as bit-exact integer arithmetic on the INT pipes, so it "
@@ -994,6 +1092,8 @@ def main():
         b1, s1 = run_oracle_sample(spec, plan1, 1)
         cpu["single_core"] = {"value": b1 / s1 / 1e9, "unit": UNIT, "cores": 1,
                               "sample": "%.0f MiB" % (b1 / 2 ** 20), "wall_s": s1}
+        if not args.no_configs:
+            cpu["configs"] = oracle_config_rates(threads)
         # the served configuration: the oracle on the captured sample, which
         # also checks every captured ciphertext byte for byte
         if served_sample:

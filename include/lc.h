@@ -450,6 +450,24 @@ typedef struct {
 lc_status lc_ctx_digit_stats(lc_ctx* ctx, int enable);
 lc_status lc_ctx_get_digit_stats(lc_ctx* ctx, lc_digit_stats_t* out);
 
+/* Byte statistics of every ciphertext the context writes, fused into the
+ * cipher kernel (Sec. 4: the histogram of Fig. 2 and the lagged products
+ * behind the auto-correlation of Fig. 3), so that no second pass reads the
+ * ciphertexts.  lc_ctx_ciphertext_stats(ctx, 1) zeroes the accumulators and
+ * makes the context's later encryptions (lc_encrypt, lc_run_batch,
+ * lc_run_batch_ex and the host-buffer batches; decryptions are not counted)
+ * run a counting build of the cipher kernel with identical outputs, 256
+ * threads per CTA; 0 stops counting.  Synchronises the device.
+ * lc_ctx_get_ciphertext_stats synchronises the device and returns the sum,
+ * over those ciphertexts C, of what lc_byte_stats(C, |C|, LC_STATS_MAX_LAG)
+ * gives: n = the ciphertext bytes, the histogram, sum, sum_sq, and lag_sum[k]
+ * = the sum of x_i x_{i+k+1} over pairs inside one ciphertext.  All zero if
+ * never enabled.  While counting, a batch whose encryptions write 2^32 or
+ * more ciphertext bytes gives LC_ERR_ARG (the kernel's per-CTA counters are
+ * 32-bit). */
+lc_status lc_ctx_ciphertext_stats(lc_ctx* ctx, int enable);
+lc_status lc_ctx_get_ciphertext_stats(lc_ctx* ctx, lc_byte_stats_t* out);
+
 /* Seeded input generator (not part of the paper's method): writes bytes
  * [offset, offset + n) of the counter-based SplitMix64 byte stream `seed`
  * (Steele, Lea & Flood 2014; byte j = byte j mod 8, little-endian, of word

@@ -25,10 +25,12 @@ size_t batch_kernel_smem(int variant);
 const void* batch_kernel_ptr(int variant);
 cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
                          const DevParams& p, const double* theta, cudaStream_t s,
-                         unsigned long long* dig = nullptr);
+                         unsigned long long* dig = nullptr, unsigned long long* ct = nullptr);
 cudaError_t launch_finalize(int grid, const uint8_t* ws, const uint32_t* scratch, uint32_t block_len,
                             cudaStream_t s);
 cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offset, cudaStream_t s);
+cudaError_t launch_ct_stats_fixup(int grid, const uint8_t* ws, uint32_t block_len, uint32_t tag_len,
+                                  unsigned long long* ct, cudaStream_t s);
 uint32_t emu_mask();
 cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsigned long long* acc,
                          int sms, cudaStream_t s);
@@ -88,6 +90,9 @@ struct lc_ctx {
   unsigned long long* stats_dev = nullptr;  // lc_byte_stats accumulators
   bool digits = false;                      // count the Fig. 1 digit statistics
   unsigned long long* digits_dev = nullptr;  // 3 * kDigBins counters
+  bool ct_stats = false;                     // accumulate the ciphertexts' byte statistics
+  unsigned long long* ct_stats_dev = nullptr;  // kCtStatsWords counters
+  uint64_t ct_stats_bytes = 0;               // ciphertext bytes counted since enabled
   cudaStream_t copy_in = nullptr, copy_out = nullptr;  // host-buffer batch copies
   HostSlot hslots[LC_HOST_INFLIGHT];
   uint64_t next_ticket = 1;
@@ -294,7 +299,8 @@ lc_status build_graph(lc_ctx* ctx, int v) {
   G.exec = nullptr;
   G.graph = nullptr;
   G.valid = false;
-  const int threads = (int)ctx->launch.threads_per_cta;
+  // the counting variants' shared-memory slots are sized for their own CTA shape
+  const int threads = variant_has_ct_stats(v) ? kCtStatsThreads : (int)ctx->launch.threads_per_cta;
   int per_sm = resident_ctas(v, threads);
   if (ctx->launch.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)ctx->launch.ctas_per_sm);
   G.grid = ctx->sm_count * per_sm;
@@ -310,10 +316,13 @@ lc_status build_graph(lc_ctx* ctx, int v) {
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.a, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
     e = launch_batch(v, G.grid, threads, ctx->ws_dev, ctx->scratch_dev, ctx->dparams, ctx->theta_dev, s,
-                     ctx->digits_dev);
+                     ctx->digits_dev, ctx->ct_stats_dev);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(ep.b, s, cudaEventRecordExternal);
   if (e == cudaSuccess)
     e = launch_finalize(kFinalizeGrid, ctx->ws_dev, ctx->scratch_dev, ctx->params.block_len, s);
+  if (e == cudaSuccess && variant_has_ct_stats(v))
+    e = launch_ct_stats_fixup(kFinalizeGrid, ctx->ws_dev, ctx->params.block_len, ctx->params.tag_len,
+                              ctx->ct_stats_dev, s);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -355,6 +364,11 @@ lc_status build_graph(lc_ctx* ctx, int v) {
 int batch_variant(const lc_ctx* ctx, size_t nrows, bool msg_k = false) {
   // a request with its own k other than (4, 4, 4) needs the general path,
   // which reads k per message
+  const bool v1 = !msg_k && ctx->variant == kVariantV1;
+  if (ctx->ct_stats) {
+    if (ctx->digits) return v1 ? kVariantV1DigitsCtStats : kVariantGeneralDigitsCtStats;
+    return v1 ? kVariantV1CtStats : kVariantGeneralCtStats;
+  }
   if (msg_k) return ctx->digits ? kVariantGeneralDigits : kVariantGeneral;
   if (ctx->digits) return ctx->variant == kVariantV1 ? kVariantV1Digits : kVariantGeneralDigits;
   if (ctx->variant != kVariantV1) return ctx->variant;
@@ -477,6 +491,15 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   const size_t nrows = ctx->h_rows.size();
   const size_t bytes = sizeof(DevHeader) + count * sizeof(DevMsg) + nrows * sizeof(DevRow) +
                        count * sizeof(int32_t);
+  // Ciphertext bytes this batch adds to the fused statistics: the CTAs'
+  // 32-bit histogram columns stay exact below 2^32 bytes per batch.
+  uint64_t ct_bytes = 0;
+  if (ctx->ct_stats) {
+    for (size_t i = 0; i < count; i++)
+      if (ctx->h_init[i] == LC_OK && !(ctx->h_msgs[i].flags & kFlagDecrypt))
+        ct_bytes += ct_len(p, (size_t)ctx->h_msgs[i].n, m);
+    if (ct_bytes > 0xFFFFFFFFull) return LC_ERR_ARG;
+  }
 
   // Device workspace (graphs are rebuilt whenever a buffer moves).
   const int v = batch_variant(ctx, nrows, msg_k);
@@ -523,7 +546,7 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   // Grid of this launch: whole CTAs per SM, as few as give every row a
   // thread in the first pass (the per-SM load stays the same), so that a
   // batch smaller than the GPU leaves CTA slots for other streams' batches.
-  const uint64_t threads = ctx->launch.threads_per_cta;
+  const uint64_t threads = variant_has_ct_stats(v) ? (uint64_t)kCtStatsThreads : ctx->launch.threads_per_cta;
   const int full_per_sm = std::max(1, G.grid / std::max(1, ctx->sm_count));
   const uint64_t need = (nrows + (uint64_t)ctx->sm_count * threads - 1) / ((uint64_t)ctx->sm_count * threads);
   const int grid = ctx->sm_count * (int)std::min<uint64_t>(std::max<uint64_t>(need, 1), (uint64_t)full_per_sm);
@@ -565,7 +588,8 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
     G.cur_grid = grid;
   }
   LC_CUDA(cudaGraphLaunch(G.exec, s));
-  ctx->launches += 2;  // cipher kernel + finalize kernel
+  ctx->launches += variant_has_ct_stats(v) ? 3 : 2;  // cipher kernel + finalize (+ statistics fix-up)
+  ctx->ct_stats_bytes += ct_bytes;
 #ifdef LC_CHECKED
   {
     // Checked build: wait for the batch and report a table index or part
@@ -722,6 +746,7 @@ void lc_ctx_destroy(lc_ctx* ctx) {
   }
   if (ctx->stats_dev) cudaFree(ctx->stats_dev);
   if (ctx->digits_dev) cudaFree(ctx->digits_dev);
+  if (ctx->ct_stats_dev) cudaFree(ctx->ct_stats_dev);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
   if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
@@ -1127,6 +1152,11 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   lc_launch bestl = saved;
   double best_ms = 1e300;
   ctx->tune_report.clear();
+  // the probe times the plain throughput variant and adds nothing to the
+  // digit or ciphertext statistics being counted
+  const bool saved_digits = ctx->digits, saved_ct = ctx->ct_stats;
+  ctx->digits = false;
+  ctx->ct_stats = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e0));
   if (st == LC_OK) st = cuda_fail(cudaEventCreate(&e1));
@@ -1170,6 +1200,8 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
   cudaStreamSynchronize(s);
   cudaFree(buf);
   ctx->launch = (st == LC_OK) ? bestl : saved;
+  ctx->digits = saved_digits;
+  ctx->ct_stats = saved_ct;
   invalidate_graphs(ctx);
   if (best) *best = ctx->launch;
   return st;
@@ -1265,6 +1297,42 @@ lc_status lc_ctx_get_digit_stats(lc_ctx* ctx, lc_digit_stats_t* out) {
   }
   for (int b = 0; b < 128; b++) out->states += out->int_part[0][b];
   out->states += out->out_of_range[0];
+  return LC_OK;
+}
+
+lc_status lc_ctx_ciphertext_stats(lc_ctx* ctx, int enable) {
+  if (!ctx) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  if (enable) {
+    const size_t bytes = kCtStatsWords * sizeof(unsigned long long);
+    if (!ctx->ct_stats_dev) {
+      LC_CUDA(cudaDeviceSynchronize());
+      LC_CUDA(cudaMalloc(&ctx->ct_stats_dev, bytes));
+      invalidate_graphs(ctx);  // the counting variants take this pointer
+    }
+    LC_CUDA(cudaDeviceSynchronize());
+    LC_CUDA(cudaMemset(ctx->ct_stats_dev, 0, bytes));
+    ctx->ct_stats_bytes = 0;
+  }
+  ctx->ct_stats = enable != 0;
+  return LC_OK;
+}
+
+lc_status lc_ctx_get_ciphertext_stats(lc_ctx* ctx, lc_byte_stats_t* out) {
+  if (!ctx || !out) return LC_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  memset(out, 0, sizeof *out);
+  if (!ctx->ct_stats_dev) return LC_OK;
+  unsigned long long h[kCtStatsWords];
+  LC_CUDA(cudaDeviceSynchronize());
+  LC_CUDA(cudaMemcpy(h, ctx->ct_stats_dev, sizeof h, cudaMemcpyDeviceToHost));
+  out->n = ctx->ct_stats_bytes;
+  for (int b = 0; b < 256; b++) {
+    out->hist[b] = h[b];
+    out->sum += (uint64_t)b * h[b];
+    out->sum_sq += (uint64_t)b * (uint64_t)b * h[b];
+  }
+  for (int k = 0; k < LC_STATS_MAX_LAG; k++) out->lag_sum[k] = h[256 + k];
   return LC_OK;
 }
 

@@ -156,6 +156,75 @@ __device__ __forceinline__ void count_state(uint32_t* dig, double x, double y, d
 }
 
 // ---------------------------------------------------------------------------
+// Fused ciphertext statistics (Sec. 4: the frequency histogram of Fig. 2 and
+// the lagged products behind the auto-correlation of Fig. 3) of the bytes an
+// encrypting thread writes, counted as they are produced.  A thread's bytes
+// form contiguous segments of the ciphertext (a part's body, then its tag);
+// the products x_i x_{i+k}, k = 1..8, with both bytes in one segment are
+// summed here, the few that span two segments by ct_stats_fixup_kernel.
+//   hist: the CTA's histogram, bin b of this lane at hist[b << 5]
+//   lag:  this thread's 64-bit accumulator of lag k at lag[(k - 1) * 256]
+//   h0, h1: the segment's last 8 bytes, oldest in the low byte of h0 (zero
+//           before the segment starts, so those products vanish)
+// ---------------------------------------------------------------------------
+struct CtStats {
+  uint32_t* hist;
+  unsigned long long* lag;
+  uint32_t h0, h1;
+
+  __device__ __forceinline__ void segment() { h0 = h1 = 0u; }
+  // one byte y
+  __device__ __forceinline__ void byte(uint32_t y) {
+    atomicAdd(hist + (y << 5), 1u);
+#pragma unroll
+    for (int k = 1; k <= LC_STATS_MAX_LAG; k++) {
+      const uint32_t w = k <= 4 ? h1 : h0;
+      const uint32_t x = (w >> (8 * ((k <= 4 ? 4 : 8) - k))) & 255u;  // the byte k places back
+      lag[(k - 1) * kCtStatsThreads] += (unsigned long long)(y * x);
+    }
+    h0 = __funnelshift_r(h0, h1, 8);
+    h1 = (h1 >> 8) | (y << 24);
+  }
+  // 16 bytes o0..o3 (little-endian words): with W = h0, h1, o0 .. o3, the
+  // partner word of W[m] at lag k starts 4m - k bytes into W; four unsigned
+  // byte dot products per lag.  One chunk adds at most 16 * 255^2 per lag.
+  __device__ __forceinline__ void chunk(uint32_t o0, uint32_t o1, uint32_t o2, uint32_t o3) {
+    const uint32_t W[6] = {h0, h1, o0, o1, o2, o3};
+#pragma unroll
+    for (int m = 2; m < 6; m++) {
+      atomicAdd(hist + ((W[m] & 255u) << 5), 1u);
+      atomicAdd(hist + (((W[m] >> 8) & 255u) << 5), 1u);
+      atomicAdd(hist + (((W[m] >> 16) & 255u) << 5), 1u);
+      atomicAdd(hist + ((W[m] >> 24) << 5), 1u);
+    }
+    // F[s][i]: bytes 4i + s .. 4i + s + 3 of W
+    uint32_t F1[5], F2[5], F3[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+      F1[i] = __funnelshift_r(W[i], W[i + 1], 8);
+      F2[i] = __funnelshift_r(W[i], W[i + 1], 16);
+      F3[i] = __funnelshift_r(W[i], W[i + 1], 24);
+    }
+    uint32_t t[LC_STATS_MAX_LAG] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int m = 2; m < 6; m++) {
+      t[0] = __dp4a(W[m], F3[m - 1], t[0]);
+      t[1] = __dp4a(W[m], F2[m - 1], t[1]);
+      t[2] = __dp4a(W[m], F1[m - 1], t[2]);
+      t[3] = __dp4a(W[m], W[m - 1], t[3]);
+      t[4] = __dp4a(W[m], F3[m - 2], t[4]);
+      t[5] = __dp4a(W[m], F2[m - 2], t[5]);
+      t[6] = __dp4a(W[m], F1[m - 2], t[6]);
+      t[7] = __dp4a(W[m], W[m - 2], t[7]);
+    }
+#pragma unroll
+    for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k * kCtStatsThreads] += (unsigned long long)t[k];
+    h0 = o2;
+    h1 = o3;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Trajectory state between bytes (Sec. 3.2).  V_i caches floor(alpha_i
 // 10^13): alpha_i only changes in Step 3, and every R_nu of the following
 // byte reads the same V_i.
@@ -313,11 +382,14 @@ __device__ __forceinline__ uint32_t sel4(uint32_t q, uint32_t v0, uint32_t v1, u
 // One trajectory: Eq. 5 plus the part offset b * eta, the warm-up, then the
 // part's body bytes and its tag.  Returns the tag verdict (always true when
 // encrypting).
-template <class Path, bool kDig>
+// kCt: count the ciphertext statistics of an encryption's output into cs.
+template <class Path, bool kDig, bool kCt>
 __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
-                        const double* __restrict__ theta, uint32_t* dig) {
+                        const double* __restrict__ theta, uint32_t* dig, CtStats& cs) {
   const bool seq = (Mg.flags & kFlagSequential) != 0;
   const uint32_t dec = (Mg.flags & kFlagDecrypt) ? 1u : 0u;
+  const bool ct = kCt && !dec;
+  if (kCt) cs.segment();
   const uint64_t lo = seq ? 0 : (uint64_t)b * p.block_len;
   const uint64_t len = seq ? Mg.n : min((uint64_t)p.block_len, Mg.n - lo);
   const uint64_t tag_off = Mg.n + (seq ? 0 : (uint64_t)b * p.tag_len);
@@ -348,7 +420,11 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
   // Tail: single bytes.
   const uint64_t head = min((uint64_t)((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u), len);
   uint64_t i = 0;
-  for (; i < head; i++) dst[i] = (uint8_t)t.template step<kDig>(src[i], dec, p, theta, dig);
+  for (; i < head; i++) {
+    const uint32_t yb = t.template step<kDig>(src[i], dec, p, theta, dig);
+    dst[i] = (uint8_t)yb;
+    if (ct) cs.byte(yb);
+  }
   const uint64_t nv = (len - head) >> 4;
   if (nv) {
     const uint8_t* s1 = src + head;
@@ -387,13 +463,19 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
         o3 = (o3 >> 8) | (yb << 24);
       }
       d4[c] = make_uint4(o0, o1, o2, o3);
+      if (ct) cs.chunk(o0, o1, o2, o3);
       cur = nxt;
     }
     i = head + (nv << 4);
   }
-  for (; i < len; i++) dst[i] = (uint8_t)t.template step<kDig>(src[i], dec, p, theta, dig);
+  for (; i < len; i++) {
+    const uint32_t yb = t.template step<kDig>(src[i], dec, p, theta, dig);
+    dst[i] = (uint8_t)yb;
+    if (ct) cs.byte(yb);
+  }
 
   // Tag: T further bytes whose plaintext is the message length, LE64(n).
+  if (kCt) cs.segment();
   bool ok = true;
   for (uint32_t q = 0; q < p.tag_len; q++) {
     const uint32_t Q = (uint32_t)(Mg.n >> (8 * q)) & 255u;
@@ -401,7 +483,9 @@ __device__ bool run_row(const DevMsg& Mg, uint32_t b, const DevParams& p,
       const uint32_t got = t.template step<kDig>(Mg.in[tag_off + q], 1u, p, theta, dig);
       ok = ok && (got == Q);
     } else {
-      Mg.out[tag_off + q] = (uint8_t)t.template step<kDig>(Q, 0u, p, theta, dig);
+      const uint32_t yb = t.template step<kDig>(Q, 0u, p, theta, dig);
+      Mg.out[tag_off + q] = (uint8_t)yb;
+      if (ct) cs.byte(yb);
     }
   }
   return ok;
@@ -418,18 +502,32 @@ __device__ __forceinline__ void load_msg(DevMsg& m, const DevMsg* src) {
 // flattened part table (sorted longest first) with warp-aggregated atomics.
 // kDig: also count the Fig. 1 digit statistics of every state after the
 // Euler step(s) of a byte into dig_g (3 * kDigBins 64-bit counters).
-template <class Path, bool kDig = false>
+// kCt: also accumulate the byte statistics of every ciphertext the batch
+// writes into ct_g (kCtStatsWords 64-bit counters; launched with
+// kCtStatsThreads threads per CTA, the dynamic shared memory holding the
+// CTA's histogram and per-thread lag sums after the Theta table).
+template <class Path, bool kDig = false, bool kCt = false>
 __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_t* __restrict__ ws,
                                                     uint32_t* __restrict__ scratch,
                                                     DevParams p,
                                                     const double* __restrict__ theta_g,
-                                                    unsigned long long* __restrict__ dig_g) {
+                                                    unsigned long long* __restrict__ dig_g,
+                                                    unsigned long long* __restrict__ ct_g) {
   extern __shared__ double s_theta[];
   __shared__ uint32_t s_dig[kDig ? 3 * kDigBins : 1];
   const int nth = Path::kThetaRows * 256;
   for (int i = threadIdx.x; i < nth; i += blockDim.x) s_theta[i] = theta_g[i];
   if constexpr (kDig) {
     for (int i = threadIdx.x; i < 3 * kDigBins; i += blockDim.x) s_dig[i] = 0u;
+  }
+  CtStats cs;
+  uint32_t* const ct_hist = reinterpret_cast<uint32_t*>(s_theta + nth);
+  unsigned long long* const ct_lag = reinterpret_cast<unsigned long long*>(ct_hist + 256 * 32);
+  if constexpr (kCt) {
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) ct_hist[i] = 0u;
+    for (int i = threadIdx.x; i < LC_STATS_MAX_LAG * kCtStatsThreads; i += blockDim.x) ct_lag[i] = 0ull;
+    cs.hist = ct_hist + (threadIdx.x & 31u);
+    cs.lag = ct_lag + threadIdx.x;
   }
   __syncthreads();
 
@@ -490,7 +588,7 @@ __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_
       }
     }
 #endif
-    const bool ok = run_row<Path, kDig>(M, row.b, p, s_theta, s_dig);
+    const bool ok = run_row<Path, kDig, kCt>(M, row.b, p, s_theta, s_dig, cs);
     if (M.flags & kFlagDecrypt) {
       // Segmented vote: threads of the warp holding parts of the same
       // message combine their verdicts; one atomic per message and warp.
@@ -504,6 +602,81 @@ __global__ void __launch_bounds__(256, Path::kMinCtas) batch_kernel(const uint8_
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * kDigBins; i += blockDim.x)
       if (s_dig[i]) atomicAdd(dig_g + i, (unsigned long long)s_dig[i]);
+  }
+  if constexpr (kCt) {
+    __syncthreads();
+    // bin b: the 32 lane columns, read from a bin-dependent column on so
+    // that the threads of a warp hit different banks
+    for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
+      unsigned long long t = 0;
+      for (uint32_t c = 0; c < 32; c++) t += ct_hist[b * 32u + ((c + b) & 31u)];
+      if (t) atomicAdd(ct_g + b, t);
+    }
+    // lag sums: warp reduction, one atomic per warp and lag
+#pragma unroll
+    for (int k = 0; k < LC_STATS_MAX_LAG; k++) {
+      unsigned long long v = ct_lag[k * kCtStatsThreads + threadIdx.x];
+      for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+      if ((threadIdx.x & 31u) == 0 && v) atomicAdd(ct_g + 256 + k, v);
+    }
+  }
+}
+
+// The lagged products x_i x_{i+k} (k = 1..LC_STATS_MAX_LAG) of an
+// encryption's ciphertext whose two bytes lie in different segments (part
+// bodies and tags, each written by its own thread).  A pair is counted at
+// the first segment start q after i: i in [max(q', q - 8), q) with q' the
+// start of i's segment, j = i + k in [q, |C|).  Row (message, b) covers the
+// segment starts b * block_len (b > 0) and n + b * tag_len (unless it is
+// the empty body's end at 0).  Runs after the cipher kernel, which wrote
+// every byte it reads.
+__global__ void ct_stats_fixup_kernel(const uint8_t* __restrict__ ws, uint32_t block_len, uint32_t tag_len,
+                                      unsigned long long* __restrict__ ct_g) {
+  const DevHeader* H = reinterpret_cast<const DevHeader*>(ws);
+  const uint32_t nrows = H->nrows;
+  const uint32_t nmsgs = H->nmsgs;
+  const DevMsg* msgs = reinterpret_cast<const DevMsg*>(ws + sizeof(DevHeader));
+  const DevRow* rows = reinterpret_cast<const DevRow*>(msgs + nmsgs);
+  unsigned long long acc[LC_STATS_MAX_LAG] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    const DevRow row = rows[r];
+#ifdef LC_CHECKED
+    if (row.msg >= nmsgs) continue;  // recorded by the cipher kernel
+#endif
+    const DevMsg& M = msgs[row.msg];
+    if (M.flags & kFlagDecrypt) continue;
+    const bool seq = (M.flags & kFlagSequential) != 0;
+    const uint64_t n = M.n;
+    const uint64_t nb = seq ? 1 : (n ? (n + block_len - 1) / block_len : 1);
+    const uint64_t clen = n + tag_len * nb;
+    const uint8_t* C = M.out;
+    uint64_t q[2], qp[2];
+    int nq = 0;
+    if (!seq && row.b > 0) {
+      q[nq] = (uint64_t)row.b * block_len;
+      qp[nq++] = (uint64_t)(row.b - 1) * block_len;
+    }
+    if (row.b > 0 || n > 0) {
+      q[nq] = n + (uint64_t)row.b * tag_len;
+      qp[nq++] = row.b > 0 ? n + (uint64_t)(row.b - 1) * tag_len : (seq ? 0 : (nb - 1) * block_len);
+    }
+    for (int e = 0; e < nq; e++) {
+      const uint64_t i0 = q[e] - qp[e] > LC_STATS_MAX_LAG ? q[e] - LC_STATS_MAX_LAG : qp[e];
+      for (uint64_t i = i0; i < q[e]; i++) {
+        const uint32_t x = C[i];
+#pragma unroll
+        for (int k = 1; k <= LC_STATS_MAX_LAG; k++) {
+          const uint64_t j = i + k;
+          if (j >= q[e] && j < clen) acc[k - 1] += (unsigned long long)(x * (uint32_t)C[j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < LC_STATS_MAX_LAG; k++) {
+    unsigned long long v = acc[k];
+    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+    if ((threadIdx.x & 31u) == 0 && v) atomicAdd(ct_g + 256 + k, v);
   }
 }
 
@@ -587,8 +760,8 @@ int kernel_variant(const DevParams& p) {
 }
 
 size_t batch_kernel_smem(int variant) {
-  const bool general = variant == kVariantGeneral || variant == kVariantGeneralDigits;
-  return (general ? kThetaEntries : 4 * 256) * sizeof(double);
+  return (variant_is_general(variant) ? kThetaEntries : 4 * 256) * sizeof(double) +
+         (variant_has_ct_stats(variant) ? kCtStatsSmem : 0);
 }
 
 const void* batch_kernel_ptr(int variant) {
@@ -599,35 +772,59 @@ const void* batch_kernel_ptr(int variant) {
     case kVariantV1Dense: return reinterpret_cast<const void*>(&batch_kernel<KV1Dense>);
     case kVariantV1Digits: return reinterpret_cast<const void*>(&batch_kernel<KV1, true>);
     case kVariantGeneralDigits: return reinterpret_cast<const void*>(&batch_kernel<KGeneral, true>);
+    case kVariantV1CtStats: return reinterpret_cast<const void*>(&batch_kernel<KV1, false, true>);
+    case kVariantGeneralCtStats: return reinterpret_cast<const void*>(&batch_kernel<KGeneral, false, true>);
+    case kVariantV1DigitsCtStats: return reinterpret_cast<const void*>(&batch_kernel<KV1, true, true>);
+    case kVariantGeneralDigitsCtStats:
+      return reinterpret_cast<const void*>(&batch_kernel<KGeneral, true, true>);
     default: return reinterpret_cast<const void*>(&batch_kernel<KV1>);
   }
 }
 
 cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
                          const DevParams& p, const double* theta, cudaStream_t s,
-                         unsigned long long* dig) {
+                         unsigned long long* dig, unsigned long long* ct) {
   const size_t smem = batch_kernel_smem(variant);
+  if (variant_has_ct_stats(variant) && (block != kCtStatsThreads || !ct)) return cudaErrorInvalidValue;
   switch (variant) {
     case kVariantGeneral:
-      batch_kernel<KGeneral><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      batch_kernel<KGeneral><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantGeneral4:
-      batch_kernel<KGeneral4><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      batch_kernel<KGeneral4><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantV1Latency:
-      batch_kernel<KV1Lat><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      batch_kernel<KV1Lat><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantV1Dense:
-      batch_kernel<KV1Dense><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      batch_kernel<KV1Dense><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantV1Digits:
-      batch_kernel<KV1, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      batch_kernel<KV1, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantGeneralDigits:
-      batch_kernel<KGeneral, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig);
+      batch_kernel<KGeneral, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
-    default: batch_kernel<KV1><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig); break;
+    case kVariantV1CtStats:
+      batch_kernel<KV1, false, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    case kVariantGeneralCtStats:
+      batch_kernel<KGeneral, false, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    case kVariantV1DigitsCtStats:
+      batch_kernel<KV1, true, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    case kVariantGeneralDigitsCtStats:
+      batch_kernel<KGeneral, true, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    default: batch_kernel<KV1><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_stats_fixup(int grid, const uint8_t* ws, uint32_t block_len, uint32_t tag_len,
+                                  unsigned long long* ct, cudaStream_t s) {
+  ct_stats_fixup_kernel<<<grid, 256, 0, s>>>(ws, block_len, tag_len, ct);
   return cudaGetLastError();
 }
 

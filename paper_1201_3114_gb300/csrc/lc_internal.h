@@ -30,11 +30,36 @@ constexpr int kVariantV1Dense = 4;
 // Fig. 1 (lc_ctx_digit_stats).
 constexpr int kVariantV1Digits = 5;
 constexpr int kVariantGeneralDigits = 6;
-constexpr int kNumVariants = 7;
+// kVariantV1 and kVariantGeneral that also accumulate the byte statistics
+// of every ciphertext they write (lc_ctx_ciphertext_stats), without and with
+// the digit statistics.
+constexpr int kVariantV1CtStats = 7;
+constexpr int kVariantGeneralCtStats = 8;
+constexpr int kVariantV1DigitsCtStats = 9;
+constexpr int kVariantGeneralDigitsCtStats = 10;
+constexpr int kNumVariants = 11;
+
+inline bool variant_has_ct_stats(int v) { return v >= kVariantV1CtStats && v <= kVariantGeneralDigitsCtStats; }
+inline bool variant_is_general(int v) {
+  return v == kVariantGeneral || v == kVariantGeneralDigits || v == kVariantGeneralCtStats ||
+         v == kVariantGeneralDigitsCtStats;
+}
 
 // Fig. 1 digit statistics: counters per coordinate (128 integer-part bins,
 // 3 x 100 digit-pair bins, 1 out-of-range count).
 constexpr int kDigBins = 429;
+
+// Fused ciphertext statistics (Sec. 4, Figs. 2-3): 64-bit accumulators
+// [0, 256) byte histogram, [256, 256 + LC_STATS_MAX_LAG) sums of x_i x_{i+k}.
+constexpr int kCtStatsWords = 256 + LC_STATS_MAX_LAG;
+// Threads per CTA of the counting variants (their shared-memory slots are
+// sized for it).
+constexpr int kCtStatsThreads = 256;
+// Shared memory of the counting variants beyond the Theta table: the CTA's
+// histogram as [bin][lane] 32-bit counters and one 64-bit accumulator per
+// thread and lag.
+constexpr size_t kCtStatsSmem = 256 * 32 * sizeof(uint32_t) +
+                                (size_t)LC_STATS_MAX_LAG * kCtStatsThreads * sizeof(unsigned long long);
 
 // Below this many parts per SM (1.5 warps per SM sub-partition) a v1 batch
 // runs the latency variant (measured crossover on GB300).

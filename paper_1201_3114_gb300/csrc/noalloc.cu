@@ -20,7 +20,7 @@
 namespace lc {
 cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, uint32_t* scratch,
                          const DevParams& p, const double* theta, cudaStream_t s,
-                         unsigned long long* dig = nullptr);
+                         unsigned long long* dig = nullptr, unsigned long long* ct = nullptr);
 cudaError_t launch_finalize(int grid, const uint8_t* ws, const uint32_t* scratch, uint32_t block_len,
                             cudaStream_t s);
 const void* batch_kernel_ptr(int variant);

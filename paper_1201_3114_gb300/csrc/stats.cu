@@ -4,20 +4,27 @@
 // auto-correlation of Fig. 3.  Every quantity is an exact integer sum, so
 // the result does not depend on the order in which threads add.
 //
-// One pass over the data, bound by HBM bandwidth.  Each CTA keeps a private
+// One pass over the data, bound by HBM bandwidth in principle and, on
+// GB300, by the shared-memory atomics of the histogram (one per byte) and
+// the integer work of the lagged products.  Each CTA keeps a private
 // histogram in shared memory laid out as [bin][lane]: lane l of every warp
 // counts into column l, so the 32 atomics of a warp instruction always fall
-// in 32 different banks.  The bytes reach the CTA as whole 16 KiB tiles that
-// one thread copies from global to shared memory with bulk asynchronous
-// copies (cp.async.bulk, completion on an mbarrier), four tiles in flight
-// per CTA, so that the loads' latency is hidden behind the counting of the
-// previous tiles.  Each thread then counts two 32-byte chunks of a tile (plus
-// the next 8 bytes for the lagged products), forming the sums of products
-// four bytes at a time with the unsigned 4-way byte dot product (__dp4a);
-// the partial sums reach the global 64-bit totals once per CTA at the end.
-// The ragged end of the buffer (less than one tile) is read with guarded
-// loads.  The sum and the sum of squares are not accumulated here: they
-// follow exactly from the histogram (the host forms them).
+// in 32 different banks.  Two kernels, each the faster one for its case on
+// GB300:
+//   - histogram only (max_lag = 0): each thread reads 32-byte chunks
+//     straight from global memory with 16-byte loads, the next chunk's loads
+//     issued before the current chunk is counted;
+//   - with lagged products: the bytes reach the CTA as 16 KiB tiles that one
+//     thread copies from global to shared memory with bulk asynchronous
+//     copies (cp.async.bulk, completion on an mbarrier), two tiles in flight
+//     per CTA.  Each thread counts two 32-byte chunks of a tile (plus the
+//     next 8 bytes for the lagged products), forming the sums of products
+//     four bytes at a time with the unsigned 4-way byte dot product
+//     (__dp4a); the partial sums reach the global 64-bit totals once per CTA
+//     at the end.
+// The ragged end of the buffer is read with guarded loads.  The sum and the
+// sum of squares are not accumulated here: they follow exactly from the
+// histogram (the host forms them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,13 +34,17 @@ namespace lc {
 
 namespace {
 
-// Chunks per thread in a staged tile and tiles in flight per CTA (chosen
-// by measurement on GB300).
+// Chunks per thread in a staged tile, tiles in flight per CTA, and the
+// resident CTAs per SM the direct kernel is compiled for (chosen by
+// measurement on GB300).
 #ifndef LC_STATS_CPT
 #define LC_STATS_CPT 2
 #endif
 #ifndef LC_STATS_STAGES
-#define LC_STATS_STAGES 4
+#define LC_STATS_STAGES 2
+#endif
+#ifndef LC_STATS_MINB
+#define LC_STATS_MINB 5
 #endif
 
 constexpr int kThreads = 256;
@@ -41,10 +52,15 @@ constexpr uint32_t kChunk = 32;                            // bytes per thread a
 constexpr int kCpt = LC_STATS_CPT;
 constexpr uint32_t kTileBytes = kCpt * kChunk * kThreads;  // bytes per staged tile
 constexpr uint32_t kCopyBytes = kTileBytes + 16;           // + the 16 bytes after it (lag partners)
-constexpr uint32_t kStageStride = kTileBytes + 128;        // keeps every stage 128-byte aligned
+constexpr uint32_t kStageStride = kCopyBytes;              // 16-byte aligned stages
 constexpr int kStages = LC_STATS_STAGES;
-constexpr uint32_t kHistBytes = 256 * 32 * 4;
-constexpr size_t kSmemBytes = kHistBytes + (size_t)kStages * kStageStride;
+constexpr size_t kSmemBytes = (size_t)kStages * kStageStride;  // dynamic: the stages
+
+// The CTA's histogram, [bin][lane]: the counter of bin x in lane l's column
+// sits at byte offset (x << 7) | (l << 2), so the 32 atomics of a warp
+// instruction fall in 32 different banks.  A static array, so that its
+// address is a constant and each count needs one shift and one and-or.
+__shared__ __align__(128) uint32_t s_hist[256 * 32];
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier waits
 constexpr int kTimeoutWord = 256;          // acc[256]: set when a wait gave up
 
@@ -94,15 +110,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// Histogram of the 32 bytes w[0..7] (all counted).
-__device__ __forceinline__ void hist_chunk(uint32_t* hl, const uint32_t (&w)[10]) {
+__device__ __forceinline__ void count_at(uint32_t off) {
+  atomicAdd(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(s_hist) + off), 1u);
+}
+
+// Histogram of the 32 bytes w[0..7] (all counted); lane4 = lane << 2.
+__device__ __forceinline__ void hist_chunk(uint32_t lane4, const uint32_t (&w)[10]) {
 #pragma unroll
   for (int j = 0; j < 8; j++) {
-    // address of bin x, column lane: x * 32 + lane words
-    atomicAdd(&hl[(w[j] & 255u) << 5], 1u);
-    atomicAdd(&hl[((w[j] >> 8) & 255u) << 5], 1u);
-    atomicAdd(&hl[((w[j] >> 16) & 255u) << 5], 1u);
-    atomicAdd(&hl[(w[j] >> 24) << 5], 1u);
+    count_at(((w[j] << 7) & 0x7F80u) | lane4);
+    count_at(((w[j] >> 1) & 0x7F80u) | lane4);
+    count_at(((w[j] >> 9) & 0x7F80u) | lane4);
+    count_at(((w[j] >> 17) & 0x7F80u) | lane4);
   }
 }
 
@@ -146,8 +165,8 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
                                                          unsigned long long* acc) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[kStages];
-  uint32_t* const hist = reinterpret_cast<uint32_t*>(smem);
-  uint8_t* const stage = smem + kHistBytes;
+  uint32_t* const hist = s_hist;
+  uint8_t* const stage = smem;
   for (int i = threadIdx.x; i < 256 * 32; i += kThreads) hist[i] = 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; s++) mbar_init(smem_addr(&bars[s]), 1u);
@@ -155,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
   }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
-  uint32_t* const hl = hist + lane;
+  const uint32_t lane4 = lane << 2;
   uint64_t lag[LC_STATS_MAX_LAG];
   uint32_t tl[LC_STATS_MAX_LAG];
 #pragma unroll
@@ -166,8 +185,9 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
   if (h && blockIdx.x == 0 && threadIdx.x == 0) {
     for (uint32_t i = 0; i < h; i++) {
       const uint32_t x = head[i];
-      atomicAdd(&hl[x * 32u], 1u);
+      count_at((x << 7) | lane4);
       if (kLags) {
+#pragma unroll
         for (uint32_t k = 1; k <= LC_STATS_MAX_LAG; k++) {
           const uint64_t j = (uint64_t)i + k;  // position in head + data
           uint32_t y = 0;
@@ -208,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
       w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
       w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
       w[8] = n8.x, w[9] = n8.y;
-      hist_chunk(hl, w);
+      hist_chunk(lane4, w);
       if (kLags) lags_chunk(w, tl);
     }
     // 32-bit partials: one tile adds kCpt x 32 products below 2^16 per lag,
@@ -249,9 +269,9 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
 #pragma unroll
       for (int j = 0; j < 10; j++) w[j] = guarded_word(data, i + 4 * j, m);
       if (i + kChunk <= m) {
-        hist_chunk(hl, w);
+        hist_chunk(lane4, w);
       } else {
-        for (uint32_t q = 0; i + q < m; q++) atomicAdd(&hl[((w[q >> 2] >> (8 * (q & 3))) & 255u) << 5], 1u);
+        for (uint32_t q = 0; i + q < m; q++) count_at((((w[q >> 2] >> (8 * (q & 3))) & 255u) << 7) | lane4);
       }
       if (kLags) lags_chunk(w, tl);
     }
@@ -280,6 +300,106 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restri
   }
 }
 
+// Direct variant: each thread reads its 32-byte chunks (and the 8 bytes
+// after each) straight from global memory with 16-byte loads, issuing the
+// next chunk's loads before it counts the current one, so that no shared
+// memory bandwidth goes to staging.  Chunks [0, nchunks) lie, with their 8
+// successors, inside the aligned part; the rest is counted by the last CTA
+// with guarded loads.  The lagged sums stay in 32-bit registers and reach
+// the 64-bit totals by global atomics: every 1024 chunks (a chunk adds less
+// than 2^21 per lag) and at the end, warp-reduced.
+template <bool kLags>
+__global__ void __launch_bounds__(kThreads, LC_STATS_MINB) stats_direct_kernel(
+    const uint8_t* __restrict__ head, uint32_t h, const uint8_t* __restrict__ data, uint64_t m,
+    uint64_t nchunks, uint32_t max_lag, unsigned long long* acc) {
+  uint32_t* const hist = s_hist;
+  for (int i = threadIdx.x; i < 256 * 32; i += kThreads) hist[i] = 0u;
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lane4 = lane << 2;
+  uint32_t tl[LC_STATS_MAX_LAG];
+#pragma unroll
+  for (int k = 0; k < LC_STATS_MAX_LAG; k++) tl[k] = 0;
+
+  if (h && blockIdx.x == 0 && threadIdx.x == 0) {
+    // the unaligned head (< 16 bytes), with partners in the aligned part
+    for (uint32_t i = 0; i < h; i++) {
+      const uint32_t x = head[i];
+      count_at((x << 7) | lane4);
+      if (kLags) {
+#pragma unroll
+        for (uint32_t k = 1; k <= LC_STATS_MAX_LAG; k++) {
+          const uint64_t j = (uint64_t)i + k;
+          uint32_t y = 0;
+          if (j < h) y = head[j];
+          else if (j - h < m) y = data[j - h];
+          tl[k - 1] += x * y;
+        }
+      }
+    }
+  }
+
+  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+  uint64_t c = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+  uint4 a = make_uint4(0, 0, 0, 0), b = a;
+  uint2 t8 = make_uint2(0, 0);
+  if (c < nchunks) {
+    const uint8_t* q = data + c * kChunk;
+    a = __ldg(reinterpret_cast<const uint4*>(q));
+    b = __ldg(reinterpret_cast<const uint4*>(q + 16));
+    t8 = __ldg(reinterpret_cast<const uint2*>(q + 32));
+  }
+  uint32_t it = 0;
+  for (; c < nchunks; c += stride) {
+    uint32_t w[10] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, t8.x, t8.y};
+    if (c + stride < nchunks) {
+      const uint8_t* q = data + (c + stride) * kChunk;
+      a = __ldg(reinterpret_cast<const uint4*>(q));
+      b = __ldg(reinterpret_cast<const uint4*>(q + 16));
+      t8 = __ldg(reinterpret_cast<const uint2*>(q + 32));
+    }
+    hist_chunk(lane4, w);
+    if (kLags) {
+      lags_chunk(w, tl);
+      if ((++it & 1023u) == 0u) {
+#pragma unroll
+        for (int k = 0; k < LC_STATS_MAX_LAG; k++) {
+          if (k < (int)max_lag) atomicAdd(acc + 258 + k, (unsigned long long)tl[k]);
+          tl[k] = 0;
+        }
+      }
+    }
+  }
+
+  if (blockIdx.x == gridDim.x - 1) {
+    for (uint64_t i = nchunks * kChunk + (uint64_t)kChunk * threadIdx.x; i < m; i += (uint64_t)kChunk * kThreads) {
+      uint32_t w[10];
+#pragma unroll
+      for (int j = 0; j < 10; j++) w[j] = guarded_word(data, i + 4 * j, m);
+      if (i + kChunk <= m) {
+        hist_chunk(lane4, w);
+      } else {
+        for (uint32_t q = 0; i + q < m; q++) count_at((((w[q >> 2] >> (8 * (q & 3))) & 255u) << 7) | lane4);
+      }
+      if (kLags) lags_chunk(w, tl);
+    }
+  }
+  __syncthreads();
+  for (uint32_t bn = threadIdx.x; bn < 256; bn += kThreads) {
+    uint64_t t = 0;
+    for (uint32_t cl = 0; cl < 32; cl++) t += hist[bn * 32u + ((cl + bn) & 31u)];
+    if (t) atomicAdd(acc + bn, (unsigned long long)t);
+  }
+  if (kLags) {
+#pragma unroll
+    for (int k = 0; k < LC_STATS_MAX_LAG; k++) {
+      unsigned long long v = tl[k];
+      for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+      if (lane == 0 && k < (int)max_lag && v) atomicAdd(acc + 258 + k, v);
+    }
+  }
+}
+
 }  // namespace
 
 // acc[256] != 0 after the kernel: a bounded wait gave up (LC_ERR_TIMEOUT).
@@ -294,9 +414,24 @@ cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsi
   // staged tiles: tile t and the 16 bytes after it lie inside the first
   // m16 = m rounded down to 16 bytes
   const uint64_t m16 = m & ~(uint64_t)15;
+  if (max_lag == 0) {
+    // histogram only: the direct kernel; chunk c reads bytes [32c, 32c + 40)
+    // of the aligned part
+    const uint64_t nchunks = m >= 40 ? (m - 8) / kChunk : 0;
+    const void* fnd = reinterpret_cast<const void*>(&stats_direct_kernel<false>);
+    int per_sm_d = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_d, fnd, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t grid_d = (uint64_t)sms * (uint64_t)(per_sm_d > 0 ? per_sm_d : 1);
+    const uint64_t need = (nchunks + kThreads - 1) / kThreads;
+    if (need < grid_d) grid_d = need;
+    if (grid_d == 0) grid_d = 1;
+    stats_direct_kernel<false><<<(unsigned)grid_d, kThreads, 0, s>>>(data, h, body, m, nchunks, 0, acc);
+    return cudaGetLastError();
+  }
+  // with lagged products: the staged kernel
   const uint64_t ntiles = m16 >= 16 ? (m16 - 16) / kTileBytes : 0;
-  const void* fn = max_lag ? reinterpret_cast<const void*>(&stats_kernel<true>)
-                           : reinterpret_cast<const void*>(&stats_kernel<false>);
+  const void* fn = reinterpret_cast<const void*>(&stats_kernel<true>);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -306,10 +441,7 @@ cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsi
   uint64_t grid = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
   if (ntiles < grid) grid = ntiles;
   if (grid == 0) grid = 1;
-  if (max_lag)
-    stats_kernel<true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(data, h, body, m, ntiles, max_lag, acc);
-  else
-    stats_kernel<false><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(data, h, body, m, ntiles, max_lag, acc);
+  stats_kernel<true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(data, h, body, m, ntiles, max_lag, acc);
   return cudaGetLastError();
 }
 

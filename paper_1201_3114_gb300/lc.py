@@ -206,6 +206,8 @@ _SIGNATURES = {
     "lc_plan_batch_ex": (C.c_int, [C.POINTER(lc_params), C.POINTER(lc_req_ex), C.c_size_t, C.c_int,
                                    C.c_void_p, C.POINTER(C.c_uint64)]),
     "lc_ctx_get_digit_stats": (C.c_int, [C.c_void_p, C.POINTER(lc_digit_stats_t)]),
+    "lc_ctx_ciphertext_stats": (C.c_int, [C.c_void_p, C.c_int]),
+    "lc_ctx_get_ciphertext_stats": (C.c_int, [C.c_void_p, C.POINTER(lc_byte_stats_t)]),
 }
 
 
@@ -590,6 +592,16 @@ def lc_ctx_digit_stats(ctx, enable: bool) -> int:
 def lc_ctx_get_digit_stats(ctx) -> lc_digit_stats_t:
     out = lc_digit_stats_t()
     check(load().lc_ctx_get_digit_stats(ctx, C.byref(out)), "lc_ctx_get_digit_stats")
+    return out
+
+
+def lc_ctx_ciphertext_stats(ctx, enable: bool) -> int:
+    return load().lc_ctx_ciphertext_stats(ctx, 1 if enable else 0)
+
+
+def lc_ctx_get_ciphertext_stats(ctx) -> lc_byte_stats_t:
+    out = lc_byte_stats_t()
+    check(load().lc_ctx_get_ciphertext_stats(ctx, C.byref(out)), "lc_ctx_get_ciphertext_stats")
     return out
 
 

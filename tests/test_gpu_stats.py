@@ -129,3 +129,84 @@ def test_fig1_digit_stats_match_oracle(over):
         assert np.array_equal(lc.lc_ctx_get_digit_stats(c.handle).arrays()[0], 2 * want_ip)
         if over.get("dt") == 0.027:
             assert int(want_oor.sum()) > 0  # the divergent profile reaches |v| >= 2^31
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4 statistics fused into the cipher kernel
+# ---------------------------------------------------------------------------
+
+def _sum_np_stats(cts):
+    """Sum over ciphertexts of their exact byte statistics (pairs inside one
+    ciphertext only)."""
+    hist = np.zeros(256, dtype=np.int64)
+    s1 = s2 = n = 0
+    lag = [0] * 8
+    for c in cts:
+        h, a, b, l8 = _np_stats(c, 8)
+        hist += h
+        s1, s2, n = s1 + a, s2 + b, n + c.size
+        lag = [x + y for x, y in zip(lag, l8)]
+    return n, hist, s1, s2, lag
+
+
+@pytest.mark.parametrize("mode", [lc.LC_PARALLEL, lc.LC_SEQUENTIAL], ids=["parallel", "sequential"])
+@pytest.mark.parametrize("over", [{}, {"k": (3, 4, 4)}, {"block_len": 16, "tag_len": 3}],
+                         ids=["v1", "general", "short-segments"])
+def test_fused_ciphertext_stats(mode, over):
+    # The counting build's statistics equal the exact statistics of the
+    # oracle's ciphertexts (encryptions only; the decryptions in the same
+    # batch add nothing), and its outputs equal the oracle's.  Sizes cover
+    # empty and one-byte messages, a last part shorter than the lag window,
+    # whole parts and ragged tails; the inputs sit at odd offsets so that
+    # the single-byte head path counts too.  block_len = 16 with 3-byte tags
+    # makes most segments shorter than 8 bytes, so pairs span several
+    # segment starts.
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    prm = O.params(**over)
+    B = prm.block_len
+    sizes = [0, 1, 5, B - 1, B, B + 3, 3 * B + 5, 4096 * 3 + 17, 70001, 262144 + 9]
+    msgs = [(synth.password(synth.subseed(90, i), 4 + (5 * i) % 29), synth.uniform_bytes(synth.subseed(91, i), n))
+            for i, n in enumerate(sizes)]
+    want_c = [O.encrypt(pw, P, mode, prm) for pw, P in msgs]
+    with lc.Context(0, lc.params(**over)) as c:
+        items, outs, keep = [], [], []
+        for i, ((pw, P), ct) in enumerate(zip(msgs, want_c)):
+            off = 1 + i % 7
+            src = torch.zeros(P.size + off, dtype=torch.uint8, device="cuda")
+            if P.size:
+                src[off:] = torch.from_numpy(P).cuda()
+            dst = torch.full((ct.size,), 0xEE, dtype=torch.uint8, device="cuda")
+            keep.append(src)
+            items.append((pw, lc.LC_ENCRYPT, src.data_ptr() + off, P.size, dst, dst.numel()))
+            outs.append(dst)
+            # a decryption of the oracle's ciphertext in the same batch
+            cin = torch.from_numpy(ct).cuda()
+            back = torch.zeros(max(1, P.size), dtype=torch.uint8, device="cuda")
+            keep += [cin, back]
+            items.append((pw, lc.LC_DECRYPT, cin, cin.numel(), back, P.size))
+        st = torch.full((len(items),), -1, dtype=torch.int32, device="cuda")
+        lc.check(lc.lc_ctx_ciphertext_stats(c.handle, True))
+        for rep in (1, 2):
+            lc.check(lc.lc_run_batch(c.handle, lc.Batch(items), st, mode))
+            got = lc.lc_ctx_get_ciphertext_stats(c.handle)
+            assert (st.cpu().numpy() == 0).all()
+            for y, ct in zip(outs, want_c):
+                assert np.array_equal(y.cpu().numpy(), ct)
+            n, hist, s1, s2, lag = _sum_np_stats(want_c)
+            assert got.n == rep * n
+            assert list(got.hist) == list(rep * hist)
+            assert (got.sum, got.sum_sq) == (rep * s1, rep * s2)
+            assert list(got.lag_sum) == [rep * x for x in lag]
+        # one message through lc_encrypt equals the separate pass over its
+        # ciphertext; counting off leaves the totals alone
+        lc.check(lc.lc_ctx_ciphertext_stats(c.handle, True))
+        pw, P = msgs[-1]
+        C1 = c.encrypt(pw, torch.from_numpy(P).cuda(), mode)
+        fused = lc.lc_ctx_get_ciphertext_stats(c.handle)
+        sep = lc.lc_byte_stats(c.handle, C1, C1.numel())
+        assert (fused.n, list(fused.hist), list(fused.lag_sum)) == (sep.n, list(sep.hist), list(sep.lag_sum))
+        lc.check(lc.lc_ctx_ciphertext_stats(c.handle, False))
+        c.encrypt(pw, torch.from_numpy(P).cuda(), mode)
+        assert lc.lc_ctx_get_ciphertext_stats(c.handle).n == sep.n
