@@ -164,20 +164,24 @@ def fp64_ops_per_launch(sizes, n_warm=3000, steps=1, B=4096, T=8):
     return ops, int(parts.sum()), int(traj_bytes.sum())
 
 
-def fp64_pipe_ops_per_launch(sizes, mask, n_warm=3000, steps=1, B=4096, T=8):
+def fp64_pipe_ops_per_launch(sizes, mask, n_warm=3000, steps=1, B=4096, T=8, warm_mask=None):
     """Binary64 operations of one launch that run on the FP64 pipe when the
-    kernel computes the operations selected by `mask` (lc_emu_mask) with
-    exact integer arithmetic: the Euler step keeps 15 minus its emulated
-    operations, each byte also has the kick, r += a' (3) and, after the
-    (mu, Omega) lock, one alpha scaling; each part 4 seeding operations."""
+    kernel computes the operations selected by `mask` (lc_emu_mask; the
+    warm-up's Euler steps by `warm_mask`, lc_warm_mask) with exact integer
+    arithmetic: the Euler step keeps 15 minus its emulated operations, each
+    byte also has the kick, r += a' (3) and, after the (mu, Omega) lock, one
+    alpha scaling; each part 4 seeding operations."""
     sizes = np.asarray(sizes, dtype=np.int64)
     parts = np.maximum(1, -(-sizes // B))
     traj_bytes = sizes + T * parts
-    emu_euler = 2 * (mask & 1) + bin(mask & 0x7FFC).count("1")
-    euler_hw = 15 - emu_euler
-    per_byte = steps * euler_hw + (0 if mask & (1 << 15) else 1) + (0 if mask & (1 << 16) else 3) \
+
+    def euler_hw(m):
+        return 15 - (2 * (m & 1) + bin(m & 0x7FFC).count("1"))
+
+    wm = mask if warm_mask is None else warm_mask
+    per_byte = steps * euler_hw(mask) + (0 if mask & (1 << 15) else 1) + (0 if mask & (1 << 16) else 3) \
         + (0 if mask & 2 else 1)
-    per_part = n_warm * euler_hw + 4
+    per_part = n_warm * euler_hw(wm) + 4
     return int(parts.sum()) * per_part + int(traj_bytes.sum()) * per_byte
 
 
@@ -581,7 +585,7 @@ def roofline_terms(sizes, kernel_ms, pipes, sm_mhz, n_warm=3000, steps=1, B=4096
     per_byte = ops / max(1, msg_bytes)
     method_gbps = min(peak_slot / per_byte, hbm / (2.0 + 8.0 * parts / max(1, msg_bytes)))
     mask = lc.lc_emu_mask()
-    hw_ops = fp64_pipe_ops_per_launch(sizes, mask, n_warm, steps, B, T)
+    hw_ops = fp64_pipe_ops_per_launch(sizes, mask, n_warm, steps, B, T, lc.lc_warm_mask())
     t_fp64 = hw_ops / (pipes.dadd_gops * 1e9) * 1e3
     rec = committed_traffic(dense_build)
     joint = None
@@ -614,12 +618,12 @@ def profile_case(args):
     lc.check(lc.lc_synth_uniform(P, n, 0x1201311400CA5E, 0, stream))
     Cb = torch.empty(ctx.ciphertext_len(n), dtype=torch.uint8, device="cuda")
     pw = b"profile-case-24-chars-pw"
+    # the throughput variant's full-grid build, whatever the case's size
+    l = lc.lc_ctx_get_launch(ctx.handle)
     if args.profile_launch:
-        tpc, dense = (int(v) for v in args.profile_launch.split(","))
-        l = lc.lc_ctx_get_launch(ctx.handle)
-        l.threads_per_cta, l.dense_build = tpc, dense
-        lc.check(lc.lc_ctx_set_launch(ctx.handle, l.threads_per_cta, l.ctas_per_sm, l.smem_staging,
-                                      l.small_batch_rows, l.host_chunk_mib, l.dense_build))
+        l.threads_per_cta, l.dense_build = (int(v) for v in args.profile_launch.split(","))
+    lc.check(lc.lc_ctx_set_launch(ctx.handle, l.threads_per_cta, l.ctas_per_sm, l.smem_staging,
+                                  l.small_batch_rows, l.host_chunk_mib, l.dense_build, 1))
     for _ in range(args.warmup):
         lc.check(lc.lc_encrypt(ctx.handle, pw, P, n, Cb, Cb.numel(), lc.LC_PARALLEL, stream))
     lc.check(lc.lc_ctx_timing(ctx.handle, True))
@@ -805,7 +809,8 @@ def main():
     ap.add_argument("--serve-batch-mib", type=int, default=256, help="bytes per served batch (cap)")
     ap.add_argument("--profile-launch", default="", metavar="THREADS,DENSE",
                     help="--profile-case: threads per CTA and dense build of the cipher kernel "
-                         "(default: the context's default launch shape)")
+                         "(default: the context's default launch shape; the case always runs the "
+                         "full-grid build of the throughput variant)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="MIB",
                     help="only time one MIB-MiB parallel-mode encryption per step (a small "
                          "case for ncu captures); prints a short JSON line")
@@ -928,8 +933,9 @@ def main():
     peak = NOMINAL_FP64_TFLOPS * 1e3 / 2.0
     traffic = committed_traffic(launch.dense_build)
     mask = lc.lc_emu_mask()
+    warm_mask = lc.lc_warm_mask()
     hw_ops = fp64_pipe_ops_per_launch(sizes, mask, prm.n_warm, prm.steps_per_byte,
-                                      prm.block_len, prm.tag_len)
+                                      prm.block_len, prm.tag_len, warm_mask)
     hw_rate = hw_ops / (kern_avg_ms * 1e-3) / 1e9
     rl_terms = roofline_terms(sizes, kern_avg_ms, pipes, clk.get("sm_mhz") or pipes.sm_clock_mhz,
                               prm.n_warm, prm.steps_per_byte, prm.block_len, prm.tag_len,
@@ -952,7 +958,7 @@ def main():
         "note": "achieved counts every binary64 operation of the path; the kernel runs the "
                 "ones in emu_mask as bit-exact integer arithmetic on the INT pipes, so it "
                 "exceeds the FP64-pipe peak; fp64_pipe_* is the part that runs on the FP64 pipe",
-        "emu_mask": hex(mask),
+        "emu_mask": hex(mask), "warm_mask": hex(warm_mask),
         "fp64_pipe_ops_per_launch": hw_ops,
         "fp64_pipe_achieved": hw_rate,
         "fp64_pipe_frac_of_probe": hw_rate / pipes.dadd_gops,

@@ -262,7 +262,13 @@ lc_status lc_wait_batch_host(lc_ctx* ctx, uint64_t ticket);
  * that one chunk's copies overlap another's kernel (0 = 4096 MiB).
  * dense_build: 1 = the throughput variant's build compiled for 4 resident
  * 256-thread CTAs per SM (at most 64 registers per thread) instead of the
- * default build for 3 (0).  None of these changes results. */
+ * default build for 3 (0).  full_grid_rows: a throughput-variant batch of
+ * at least this many parts fills the persistent grid and runs the build
+ * that also moves the kick of Step 2 to the integer pipes (lc_emu_mask);
+ * a smaller batch, whose grid is cut to fewer CTAs per SM, runs the build
+ * that keeps it on the FP64 pipe (lc_partial_mask), whose shorter
+ * dependency chains suit fewer resident warps (0 = auto: the threads of
+ * the full persistent grid).  None of these changes results. */
 typedef struct {
   uint32_t threads_per_cta;
   uint32_t ctas_per_sm;
@@ -270,6 +276,7 @@ typedef struct {
   uint32_t small_batch_rows;
   uint32_t host_chunk_mib;
   uint32_t dense_build;
+  uint32_t full_grid_rows;
 } lc_launch;
 
 lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out);
@@ -404,9 +411,14 @@ enum {
 lc_status lc_softfp_eval(uint32_t op, const uint64_t* a_dev, const uint64_t* b_dev, uint64_t* sw_dev,
                          uint64_t* hw_dev, size_t n, void* stream);
 
-/* The binary64 operations the v1 kernel computes on the integer pipe, as a
- * bit mask fixed at build time (diagnostic). */
+/* The binary64 operations the v1 kernel computes on the integer pipe, as
+ * bit masks fixed at build time (diagnostic): lc_emu_mask for the byte
+ * steps of full-grid batches, lc_partial_mask for those of smaller batches
+ * of the throughput variant, lc_warm_mask for the Euler steps of the
+ * warm-up. */
 uint32_t lc_emu_mask(void);
+uint32_t lc_partial_mask(void);
+uint32_t lc_warm_mask(void);
 
 /* Byte statistics of a device buffer, for the ciphertext analysis of
  * Sec. 4: the frequency histogram (Fig. 2; the Shannon entropy

@@ -32,6 +32,8 @@ cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offse
 cudaError_t launch_ct_stats_fixup(int grid, const uint8_t* ws, uint32_t block_len, uint32_t tag_len,
                                   unsigned long long* ct, cudaStream_t s);
 uint32_t emu_mask();
+uint32_t warm_mask();
+uint32_t partial_mask();
 cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsigned long long* acc,
                          int sms, cudaStream_t s);
 }  // namespace lc
@@ -115,7 +117,7 @@ struct lc_ctx {
     int cur_grid = 0;  // CTAs the executable graph launches now
   } graphs[kNumVariants];
 
-  lc_launch launch{256, 0, 0, 0, 0, 0};
+  lc_launch launch{256, 0, 0, 0, 0, 0, 0};
   std::vector<lc_tune_entry> tune_report;  // the last lc_tune's candidates
 
   std::unordered_map<std::string, HostKey> keys;
@@ -375,7 +377,16 @@ int batch_variant(const lc_ctx* ctx, size_t nrows, bool msg_k = false) {
   const uint64_t thr = ctx->launch.small_batch_rows ? ctx->launch.small_batch_rows
                                                     : (uint64_t)ctx->sm_count * kSmallBatchRowsPerSm;
   if (nrows < thr) return kVariantV1Latency;
-  return ctx->launch.dense_build ? kVariantV1Dense : kVariantV1;
+  const int full = ctx->launch.dense_build ? kVariantV1Dense : kVariantV1;
+  // a batch that does not fill the persistent grid runs on fewer CTAs per SM
+  uint64_t fill = ctx->launch.full_grid_rows;
+  if (!fill) {
+    const int threads = (int)ctx->launch.threads_per_cta;
+    int per_sm = resident_ctas(full, threads);
+    if (ctx->launch.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)ctx->launch.ctas_per_sm);
+    fill = (uint64_t)ctx->sm_count * (uint64_t)per_sm * (uint64_t)threads;
+  }
+  return nrows < fill ? kVariantV1Partial : full;
 }
 
 // Host validation of one request; LC_OK or the request's status code.
@@ -1169,7 +1180,7 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
       if (maxc > 1) cands.push_back((uint32_t)(maxc - 1));
       for (uint32_t c : cands) {
         // small_batch_rows = 1: the probe runs the throughput variant
-        ctx->launch = lc_launch{tpc, c, 0, 1, saved.host_chunk_mib, dense};
+        ctx->launch = lc_launch{tpc, c, 0, 1, saved.host_chunk_mib, dense, saved.full_grid_rows};
         invalidate_graphs(ctx);
         st = run_batch_impl(ctx, reqs.data(), count, stat, LC_PARALLEL, s);  // graph build, warm-up
         if (st != LC_OK) break;
@@ -1186,7 +1197,7 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
         if (st != LC_OK) break;
         std::sort(ms3.begin(), ms3.end());
         const double med = ms3[1];
-        lc_launch rec{tpc, c, 0, saved.small_batch_rows, saved.host_chunk_mib, dense};
+        lc_launch rec{tpc, c, 0, saved.small_batch_rows, saved.host_chunk_mib, dense, saved.full_grid_rows};
         ctx->tune_report.push_back(lc_tune_entry{rec, med});
         if (med < best_ms) {
           best_ms = med;
@@ -1236,6 +1247,8 @@ lc_status lc_ctx_kernel_time(lc_ctx* ctx, double* total_ms, uint64_t* launches) 
 uint64_t lc_ctx_launch_count(const lc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 uint32_t lc_emu_mask(void) { return emu_mask(); }
+uint32_t lc_warm_mask(void) { return warm_mask(); }
+uint32_t lc_partial_mask(void) { return partial_mask(); }
 
 lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t max_lag,
                         lc_byte_stats_t* out, void* stream) {

@@ -22,14 +22,22 @@
 #include "softfp64.cuh"
 
 // Binary64 operations of the v1 fast path computed on the integer pipe
-// (bit mask, see kEmu* below).  Chosen by measurement on GB300.
+// (bit mask, see kEmu* below): the eight Euler multiplies, the alpha
+// scaling and the kick.  Chosen by measurement on GB300.
 #ifndef LC_EMU_MASK
-#define LC_EMU_MASK 0xFFu
+#define LC_EMU_MASK 0x80FFu
 #endif
 // The same for the warm-up steps before the first byte (they carry no
-// per-byte bookkeeping, so their best split can differ).
+// per-byte bookkeeping, so their best split can differ): the eight
+// multiplies.
 #ifndef LC_WARM_MASK
-#define LC_WARM_MASK LC_EMU_MASK
+#define LC_WARM_MASK 0xFFu
+#endif
+// The byte steps of batches that leave the persistent grid partly empty:
+// the eight multiplies and the alpha scaling (the emulated kick lengthens
+// each byte's chain, which fewer resident warps cannot hide).
+#ifndef LC_PARTIAL_MASK
+#define LC_PARTIAL_MASK 0xFFu
 #endif
 // Minimum resident 256-thread CTAs per SM the v1 kernel is compiled for
 // (bounds its registers per thread).  Chosen by measurement on GB300.
@@ -746,6 +754,7 @@ using KV1Lat = V1Path<0u>;
 // The throughput variant compiled for 4 resident 256-thread CTAs per SM (at
 // most 64 registers per thread): one of the autotuner's candidates.
 using KV1Dense = V1Path<LC_EMU_MASK, 4>;
+using KV1Partial = V1Path<LC_PARTIAL_MASK>;
 
 }  // namespace
 
@@ -770,6 +779,7 @@ const void* batch_kernel_ptr(int variant) {
     case kVariantGeneral4: return reinterpret_cast<const void*>(&batch_kernel<KGeneral4>);
     case kVariantV1Latency: return reinterpret_cast<const void*>(&batch_kernel<KV1Lat>);
     case kVariantV1Dense: return reinterpret_cast<const void*>(&batch_kernel<KV1Dense>);
+    case kVariantV1Partial: return reinterpret_cast<const void*>(&batch_kernel<KV1Partial>);
     case kVariantV1Digits: return reinterpret_cast<const void*>(&batch_kernel<KV1, true>);
     case kVariantGeneralDigits: return reinterpret_cast<const void*>(&batch_kernel<KGeneral, true>);
     case kVariantV1CtStats: return reinterpret_cast<const void*>(&batch_kernel<KV1, false, true>);
@@ -798,6 +808,9 @@ cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, ui
       break;
     case kVariantV1Dense:
       batch_kernel<KV1Dense><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    case kVariantV1Partial:
+      batch_kernel<KV1Partial><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantV1Digits:
       batch_kernel<KV1, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
@@ -843,5 +856,7 @@ cudaError_t launch_synth(uint8_t* dst, uint64_t n, uint64_t seed, uint64_t offse
 }
 
 uint32_t emu_mask() { return LC_EMU_MASK; }
+uint32_t warm_mask() { return LC_WARM_MASK; }
+uint32_t partial_mask() { return LC_PARTIAL_MASK; }
 
 }  // namespace lc

@@ -37,7 +37,10 @@ constexpr int kVariantV1CtStats = 7;
 constexpr int kVariantGeneralCtStats = 8;
 constexpr int kVariantV1DigitsCtStats = 9;
 constexpr int kVariantGeneralDigitsCtStats = 10;
-constexpr int kNumVariants = 11;
+// kVariantV1 for batches that do not fill the persistent grid: the kick
+// stays on the FP64 pipe (shorter chains for fewer resident warps).
+constexpr int kVariantV1Partial = 11;
+constexpr int kNumVariants = 12;
 
 inline bool variant_has_ct_stats(int v) { return v >= kVariantV1CtStats && v <= kVariantGeneralDigitsCtStats; }
 inline bool variant_is_general(int v) {

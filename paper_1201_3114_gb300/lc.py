@@ -78,6 +78,7 @@ class lc_launch(C.Structure):
         ("small_batch_rows", C.c_uint32),
         ("host_chunk_mib", C.c_uint32),
         ("dense_build", C.c_uint32),
+        ("full_grid_rows", C.c_uint32),
     ]
 
     def as_dict(self):
@@ -197,6 +198,8 @@ _SIGNATURES = {
     "lc_softfp_eval": (C.c_int, [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_size_t, C.c_void_p]),
     "lc_emu_mask": (C.c_uint32, []),
+    "lc_warm_mask": (C.c_uint32, []),
+    "lc_partial_mask": (C.c_uint32, []),
     "lc_byte_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32,
                                 C.POINTER(lc_byte_stats_t), C.c_void_p]),
     "lc_synth_uniform": (C.c_int, [C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint64, C.c_void_p]),
@@ -489,9 +492,9 @@ def lc_ctx_get_launch(ctx) -> lc_launch:
 
 
 def lc_ctx_set_launch(ctx, threads_per_cta=256, ctas_per_sm=0, smem_staging=0,
-                      small_batch_rows=0, host_chunk_mib=0, dense_build=0) -> int:
+                      small_batch_rows=0, host_chunk_mib=0, dense_build=0, full_grid_rows=0) -> int:
     l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, small_batch_rows, host_chunk_mib,
-                  dense_build)
+                  dense_build, full_grid_rows)
     return load().lc_ctx_set_launch(ctx, C.byref(l))
 
 
@@ -607,6 +610,14 @@ def lc_ctx_get_ciphertext_stats(ctx) -> lc_byte_stats_t:
 
 def lc_emu_mask() -> int:
     return load().lc_emu_mask()
+
+
+def lc_warm_mask() -> int:
+    return load().lc_warm_mask()
+
+
+def lc_partial_mask() -> int:
+    return load().lc_partial_mask()
 
 
 def lc_synth_uniform(dst, n, seed, offset=0, stream=None) -> int:

@@ -363,10 +363,11 @@ def test_launch_shapes_do_not_change_results(ctx):
     want = O.encrypt(pw, P)
     try:
         for tpc, cps in ((32, 1), (64, 0), (128, 2), (256, 0), (256, 4)):
-            # integer-split variant (default and dense build), FP64-only variant
-            for small, dense in ((1, 0), (1, 1), (0xFFFFFFFF, 0)):
-                assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small, 0, dense) == lc.LC_OK
-                assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small, dense)
+            # integer-split variant (full-grid build: default and dense; the
+            # partial-grid build), FP64-only variant
+            for small, dense, full in ((1, 0, 1), (1, 1, 1), (1, 0, 0), (0xFFFFFFFF, 0, 0)):
+                assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small, 0, dense, full) == lc.LC_OK
+                assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small, dense, full)
         assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 1, 0) == lc.LC_ERR_ARG
         assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, 0, 0, 2) == lc.LC_ERR_ARG
         best = lc.lc_tune(ctx.handle, 8 << 20)
@@ -382,12 +383,14 @@ def test_launch_shapes_do_not_change_results(ctx):
         lc.lc_ctx_set_launch(ctx.handle, 256, 0)
 
 
-@pytest.mark.parametrize("small", [1, 0xFFFFFFFF], ids=["int-split", "fp64-only"])
-def test_both_v1_kernel_variants(ctx, small):
-    # The batched kernel has two v1 variants (binary64 multiplies on the
-    # integer pipes, or everything on the FP64 pipe); force each one.
+@pytest.mark.parametrize("small,full", [(1, 1), (1, 0), (0xFFFFFFFF, 0)],
+                         ids=["int-split-full-grid", "int-split-partial-grid", "fp64-only"])
+def test_both_v1_kernel_variants(ctx, small, full):
+    # The batched kernel has three v1 builds: binary64 multiplies (and, on a
+    # full grid, the kick) on the integer pipes, or everything on the FP64
+    # pipe; force each one.
     try:
-        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, small) == lc.LC_OK
+        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, small, 0, 0, full) == lc.LC_OK
         for i, n in enumerate([0, 1, 17, B - 1, B + 1, 5 * B + 3]):
             for mode in (lc.LC_PARALLEL, lc.LC_SEQUENTIAL):
                 pw = synth.password(synth.subseed(60, i), 2 + 5 * i)
