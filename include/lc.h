@@ -260,9 +260,9 @@ lc_status lc_wait_batch_host(lc_ctx* ctx, uint64_t ticket);
  * (192 parts per SM).  host_chunk_mib: a host-buffer batch whose inputs
  * exceed this many MiB is cut into up to 4 chunks of whole requests, so
  * that one chunk's copies overlap another's kernel (0 = 4096 MiB).
- * dense_build: 1 = the throughput variant's build compiled for 4 resident
+ * dense_build: 1 = the throughput variant's builds compiled for 4 resident
  * 256-thread CTAs per SM (at most 64 registers per thread) instead of the
- * default build for 3 (0).  full_grid_rows: a throughput-variant batch of
+ * default builds for 3 (0).  full_grid_rows: a throughput-variant batch of
  * at least this many parts fills the persistent grid and runs the build
  * that also moves the kick of Step 2 to the integer pipes (lc_emu_mask);
  * a smaller batch, whose grid is cut to fewer CTAs per SM, runs the build

@@ -386,7 +386,8 @@ int batch_variant(const lc_ctx* ctx, size_t nrows, bool msg_k = false) {
     if (ctx->launch.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)ctx->launch.ctas_per_sm);
     fill = (uint64_t)ctx->sm_count * (uint64_t)per_sm * (uint64_t)threads;
   }
-  return nrows < fill ? kVariantV1Partial : full;
+  if (nrows >= fill) return full;
+  return ctx->launch.dense_build ? kVariantV1PartialDense : kVariantV1Partial;
 }
 
 // Host validation of one request; LC_OK or the request's status code.

@@ -755,6 +755,7 @@ using KV1Lat = V1Path<0u>;
 // most 64 registers per thread): one of the autotuner's candidates.
 using KV1Dense = V1Path<LC_EMU_MASK, 4>;
 using KV1Partial = V1Path<LC_PARTIAL_MASK>;
+using KV1PartialDense = V1Path<LC_PARTIAL_MASK, 4>;
 
 }  // namespace
 
@@ -780,6 +781,7 @@ const void* batch_kernel_ptr(int variant) {
     case kVariantV1Latency: return reinterpret_cast<const void*>(&batch_kernel<KV1Lat>);
     case kVariantV1Dense: return reinterpret_cast<const void*>(&batch_kernel<KV1Dense>);
     case kVariantV1Partial: return reinterpret_cast<const void*>(&batch_kernel<KV1Partial>);
+    case kVariantV1PartialDense: return reinterpret_cast<const void*>(&batch_kernel<KV1PartialDense>);
     case kVariantV1Digits: return reinterpret_cast<const void*>(&batch_kernel<KV1, true>);
     case kVariantGeneralDigits: return reinterpret_cast<const void*>(&batch_kernel<KGeneral, true>);
     case kVariantV1CtStats: return reinterpret_cast<const void*>(&batch_kernel<KV1, false, true>);
@@ -811,6 +813,9 @@ cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, ui
       break;
     case kVariantV1Partial:
       batch_kernel<KV1Partial><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    case kVariantV1PartialDense:
+      batch_kernel<KV1PartialDense><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantV1Digits:
       batch_kernel<KV1, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);

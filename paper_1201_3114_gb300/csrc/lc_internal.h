@@ -40,7 +40,9 @@ constexpr int kVariantGeneralDigitsCtStats = 10;
 // kVariantV1 for batches that do not fill the persistent grid: the kick
 // stays on the FP64 pipe (shorter chains for fewer resident warps).
 constexpr int kVariantV1Partial = 11;
-constexpr int kNumVariants = 12;
+// kVariantV1Partial compiled for 4 resident 256-thread CTAs per SM.
+constexpr int kVariantV1PartialDense = 12;
+constexpr int kNumVariants = 13;
 
 inline bool variant_has_ct_stats(int v) { return v >= kVariantV1CtStats && v <= kVariantGeneralDigitsCtStats; }
 inline bool variant_is_general(int v) {

@@ -146,16 +146,18 @@ class CudaBackend:
     the device goes through these methods."""
 
     def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
-                 max_batch_requests=8192, seed=0x5E4E):
+                 max_batch_requests=8192, seed=0x5E4E, dense_build=1):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
         self.ctxs = [lc.Context(device) for _ in range(streams)]
         # Batches on different streams share the GPU, so even a small batch
-        # runs the throughput (integer-split) kernel variant.
+        # runs the throughput (integer-split) kernel variant, in its dense
+        # build: 4 resident CTAs per SM let two right-sized batches (2 CTAs
+        # per SM each) run side by side.
         for c in self.ctxs:
-            lc.check(lc.lc_ctx_set_launch(c.handle, 256, 0, 0, 1), "lc_ctx_set_launch")
+            lc.check(lc.lc_ctx_set_launch(c.handle, 256, 0, 0, 1, 0, dense_build), "lc_ctx_set_launch")
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.arena = Arena(budget_bytes, self.device)
         self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
@@ -309,12 +311,12 @@ class Server:
     def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
                  max_batch_bytes=256 << 20, max_batch_requests=8192, replay_cap_bytes=None,
                  seed=0x5E4E, backend=None, policy="small_first", max_adaptive_bytes=None,
-                 backlog_batches=4):
+                 backlog_batches=4, dense_build=1):
         if policy not in ("fifo", "small_first"):
             raise ValueError("policy must be 'fifo' or 'small_first'")
         self.policy = policy
         self.be = backend if backend is not None else CudaBackend(
-            device, streams, budget_bytes, pool_bytes, max_batch_requests, seed)
+            device, streams, budget_bytes, pool_bytes, max_batch_requests, seed, dense_build)
         self.arena = self.be.arena
         self.max_batch_bytes = max_batch_bytes
         # Under a backlog (more than backlog_batches caps per slot waiting) a batch

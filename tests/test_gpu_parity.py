@@ -363,9 +363,9 @@ def test_launch_shapes_do_not_change_results(ctx):
     want = O.encrypt(pw, P)
     try:
         for tpc, cps in ((32, 1), (64, 0), (128, 2), (256, 0), (256, 4)):
-            # integer-split variant (full-grid build: default and dense; the
-            # partial-grid build), FP64-only variant
-            for small, dense, full in ((1, 0, 1), (1, 1, 1), (1, 0, 0), (0xFFFFFFFF, 0, 0)):
+            # integer-split variant (full-grid and partial-grid builds, each
+            # default and dense), FP64-only variant
+            for small, dense, full in ((1, 0, 1), (1, 1, 1), (1, 0, 0), (1, 1, 0), (0xFFFFFFFF, 0, 0)):
                 assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small, 0, dense, full) == lc.LC_OK
                 assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small, dense, full)
         assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 1, 0) == lc.LC_ERR_ARG
