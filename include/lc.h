@@ -351,6 +351,15 @@ typedef struct {
 } lc_pipe_rates;
 lc_status lc_probe_pipes(int device, lc_pipe_rates* out);
 
+/* Issue interval of binary64 adds for few warps (not part of the paper's
+ * method; it explains the latency of one trajectory): one CTA of `warps`
+ * warps (1..32) on `device`, the first `lanes` lanes (1..32) of each warp
+ * running `chains` (1, 2, 4 or 8) independent chains of dependent DADDs.
+ * *cycles receives the SM clock cycles per DADD warp instruction of the
+ * slowest warp.  Synchronises the device. */
+lc_status lc_probe_fp64_warp(int device, uint32_t warps, uint32_t chains, uint32_t lanes,
+                             double* cycles);
+
 /* Allocation-free batched path.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they
  * encrypt or decrypt -- for example code whose device memory is entirely

@@ -121,7 +121,67 @@ double time_ms(F launch, cudaStream_t s) {
   return ms;
 }
 
+// One CTA of `warps` warps; in each warp the first `lanes` lanes run K
+// independent chains of n dependent DADDs.  Each warp records its cycle
+// count (clock64) for the loop.
+template <int K>
+__global__ void probe_fp64_warp(double* out, long long* cyc, int n, int lanes, double c) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double a[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) a[k] = threadIdx.x * 1e-3 + k;
+  __syncthreads();
+  const long long t0 = clock64();
+  if (lane < lanes) {
+    for (int i = 0; i < n; i++) {
+#pragma unroll
+      for (int k = 0; k < K; k++) a[k] = __dadd_rn(a[k], c);
+    }
+  }
+  const long long t1 = clock64();
+  double s = 0;
+#pragma unroll
+  for (int k = 0; k < K; k++) s += a[k];
+  if (s == 12345.678) out[0] = s;
+  if (lane == 0) cyc[warp] = t1 - t0;
+}
+
 }  // namespace
+
+extern "C" lc_status lc_probe_fp64_warp(int device, uint32_t warps, uint32_t chains, uint32_t lanes,
+                                        double* cycles) {
+  if (!cycles || warps < 1 || warps > 32 || lanes < 1 || lanes > 32 ||
+      (chains != 1 && chains != 2 && chains != 4 && chains != 8))
+    return LC_ERR_ARG;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return LC_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return LC_ERR_CUDA;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 64 + 32 * sizeof(long long)) != cudaSuccess) {
+    cudaSetDevice(prev);
+    return LC_ERR_CUDA;
+  }
+  double* d = static_cast<double*>(buf);
+  long long* cyc = reinterpret_cast<long long*>(static_cast<char*>(buf) + 64);
+  const int n = 20000, threads = 32 * (int)warps;
+  for (int rep = 0; rep < 2; rep++) {  // the first run warms up
+    switch (chains) {
+      case 1: probe_fp64_warp<1><<<1, threads>>>(d, cyc, n, (int)lanes, 1e-9); break;
+      case 2: probe_fp64_warp<2><<<1, threads>>>(d, cyc, n, (int)lanes, 1e-9); break;
+      case 4: probe_fp64_warp<4><<<1, threads>>>(d, cyc, n, (int)lanes, 1e-9); break;
+      default: probe_fp64_warp<8><<<1, threads>>>(d, cyc, n, (int)lanes, 1e-9); break;
+    }
+  }
+  long long h[32];
+  cudaError_t e = cudaMemcpy(h, cyc, warps * sizeof(long long), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return LC_ERR_CUDA;
+  long long mx = 0;
+  for (uint32_t w = 0; w < warps; w++) mx = h[w] > mx ? h[w] : mx;
+  *cycles = (double)mx / ((double)n * chains);
+  return LC_OK;
+}
 
 extern "C" lc_status lc_probe_pipes(int device, lc_pipe_rates* out) {
   if (!out) return LC_ERR_ARG;

@@ -200,6 +200,7 @@ _SIGNATURES = {
     "lc_emu_mask": (C.c_uint32, []),
     "lc_warm_mask": (C.c_uint32, []),
     "lc_partial_mask": (C.c_uint32, []),
+    "lc_probe_fp64_warp": (C.c_int, [C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_double)]),
     "lc_byte_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32,
                                 C.POINTER(lc_byte_stats_t), C.c_void_p]),
     "lc_synth_uniform": (C.c_int, [C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint64, C.c_void_p]),
@@ -618,6 +619,12 @@ def lc_warm_mask() -> int:
 
 def lc_partial_mask() -> int:
     return load().lc_partial_mask()
+
+
+def lc_probe_fp64_warp(device, warps, chains, lanes) -> float:
+    v = C.c_double()
+    check(load().lc_probe_fp64_warp(device, warps, chains, lanes, C.byref(v)), "lc_probe_fp64_warp")
+    return v.value
 
 
 def lc_synth_uniform(dst, n, seed, offset=0, stream=None) -> int:

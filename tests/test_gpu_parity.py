@@ -770,3 +770,17 @@ def test_per_request_lambda_and_k(ctx, mode, k_in_batch):
     lc.check(lc.lc_run_batch_ex(ctx.handle, lc.BatchEx([(pw, 1, x, ct.size, y, P.size, None, (4, 3, 3))]),
                                 s1, mode))
     assert host(s1)[0] == lc.LC_ERR_INTEGRITY and not host(y).any()
+
+
+def test_pipe_probes_report_rates():
+    # The microbenchmarks behind the roofline denominators and the
+    # one-trajectory latency: positive rates; one DADD warp instruction per
+    # warp issue interval whatever the number of active lanes.
+    r = lc.lc_probe_pipes(0)
+    assert r.sm_count > 0 and r.dadd_gops > 0 and r.ialu_gops > r.dadd_gops
+    full = lc.lc_probe_fp64_warp(0, 1, 1, 32)
+    one = lc.lc_probe_fp64_warp(0, 1, 1, 1)
+    assert full > 4 and abs(full - one) / full < 0.1
+    assert lc.lc_probe_fp64_warp(0, 8, 2, 32) > full  # eight warps share the SM's FP64 pipe
+    with pytest.raises(lc.LcError):
+        lc.lc_probe_fp64_warp(0, 33, 1, 32)
