@@ -442,10 +442,17 @@ def test_config3_1gib_complete(ctx):
     P = oracle_mt.uniform(seed, n)
     want = oracle_mt.encrypt(pw, P)
     Pd = torch.from_numpy(P).cuda()
-    got = host(ctx.encrypt(pw, Pd))
-    assert got.size == want.size == n + T * (n // B)
-    assert oracle_mt.first_difference(got, want) == -1
-    del got
+    try:
+        # the default launch shape, then the dense build the autotuner
+        # usually picks for the benchmark
+        for shape in ((256, 0, 0, 0, 0, 0), (64, 0, 0, 0, 0, 1)):
+            assert lc.lc_ctx_set_launch(ctx.handle, *shape) == lc.LC_OK
+            got = host(ctx.encrypt(pw, Pd))
+            assert got.size == want.size == n + T * (n // B)
+            assert oracle_mt.first_difference(got, want) == -1, shape
+            del got
+    finally:
+        lc.lc_ctx_set_launch(ctx.handle, 256, 0)
     st, back = ctx.decrypt(pw, torch.from_numpy(want).cuda())
     assert st == lc.LC_OK
     assert torch.equal(back, Pd)
@@ -479,13 +486,24 @@ def test_config4_batch_complete(ctx):
     dout = torch.full((out_off[-1] + want[-1].size + 256,), 0xA5, dtype=torch.uint8, device="cuda")
     items = [(pws[m], dirs[m], din.data_ptr() + in_off[m], ins[m].size, dout.data_ptr() + out_off[m],
               want[m].size) for m in range(count)]
-    status = torch.full((count,), -1, dtype=torch.int32, device="cuda")
-    lc.check(lc.lc_run_batch(ctx.handle, lc.Batch(items), status))
-    assert (host(status) == 0).all()
-    hout = host(dout)
-    bad = [m for m in range(count)
-           if not np.array_equal(hout[out_off[m]:out_off[m] + want[m].size], want[m])]
-    assert not bad, bad[:10]
+    batch = lc.Batch(items)
+    try:
+        # the default launch shape, and the one the benchmark times: the
+        # autotuner's choice on a probe of this batch's size
+        for tune in (False, True):
+            lc.lc_ctx_set_launch(ctx.handle, 256, 0)
+            if tune:
+                lc.lc_tune(ctx.handle, int(sizes.sum()))
+            dout.fill_(0xA5)
+            status = torch.full((count,), -1, dtype=torch.int32, device="cuda")
+            lc.check(lc.lc_run_batch(ctx.handle, batch, status))
+            assert (host(status) == 0).all()
+            hout = host(dout)
+            bad = [m for m in range(count)
+                   if not np.array_equal(hout[out_off[m]:out_off[m] + want[m].size], want[m])]
+            assert not bad, (tune, lc.lc_ctx_get_launch(ctx.handle).as_dict(), bad[:10])
+    finally:
+        lc.lc_ctx_set_launch(ctx.handle, 256, 0)
 
 
 def test_n_it_steps_per_byte_profile():
