@@ -323,8 +323,8 @@ def reference_arm(args):
 # our arm
 # ---------------------------------------------------------------------------
 
-def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_batch_mib=256,
-                low_seconds=15.0, capture_per_class=125):
+def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_batch_mib=128,
+                low_seconds=15.0, capture_per_class=125, streams=6):
     """The served configuration (Poisson arrivals, log-uniform 256 B - 16 MiB,
     50/50, 2 % tampered decrypts, 48 GiB admission budget) for `seconds` of
     arrivals, then a supplementary run of `low_seconds` at 0.8x the measured
@@ -334,7 +334,7 @@ def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_
     stream); returns (records, sample) where sample lists each captured
     request's password, plaintext location in the seeded pool and output."""
     from paper_1201_3114_gb300 import serve, synth
-    srv = serve.Server(device, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
+    srv = serve.Server(device, streams=streams, budget_bytes=48 << 30, pool_bytes=1 << 30,
                        max_batch_bytes=max_batch_mib << 20, policy=policy)
     out = {}
     sample = None
@@ -355,6 +355,7 @@ def run_serving(seconds, rate, device, capacity_gbps, policy="small_first", max_
                     "encrypts_ok", "plaintext_checked", "plaintext_mismatches", "max_batch_bytes")
             rec = {k: st[k] for k in keep}
             rec["policy"] = policy
+            rec["streams"] = streams
             rec["rate_req_per_s"] = r
             rec["served_over_per_message"] = None
             out[label] = rec
@@ -806,7 +807,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-policy", default="small_first", choices=["small_first", "fifo"],
                     help="order in which waiting requests fill a batch")
-    ap.add_argument("--serve-batch-mib", type=int, default=256, help="bytes per served batch (cap)")
+    ap.add_argument("--serve-batch-mib", type=int, default=128, help="bytes per served batch (cap)")
+    ap.add_argument("--serve-streams", type=int, default=6, help="stream slots of the server")
     ap.add_argument("--profile-launch", default="", metavar="THREADS,DENSE",
                     help="--profile-case: threads per CTA and dense build of the cipher kernel "
                          "(default: the context's default launch shape; the case always runs the "
@@ -1083,7 +1085,7 @@ def main():
     if rank == 0 and args.serve_seconds > 0:
         served, served_sample = run_serving(args.serve_seconds, args.serve_rate, local, value / ws,
                                             args.serve_policy, args.serve_batch_mib,
-                                            args.serve_low_seconds, args.serve_capture)
+                                            args.serve_low_seconds, args.serve_capture, args.serve_streams)
 
     # ---- CPU oracle baseline
     cpu = None

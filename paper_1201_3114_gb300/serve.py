@@ -145,7 +145,7 @@ class CudaBackend:
     the device-resident plaintext pool.  Every operation the loop needs from
     the device goes through these methods."""
 
-    def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
+    def __init__(self, device=0, streams=6, budget_bytes=48 << 30, pool_bytes=1 << 30,
                  max_batch_requests=8192, seed=0x5E4E, dense_build=1):
         import torch
         self.torch = torch
@@ -308,8 +308,8 @@ class Server:
     """Continuous-batching request loop over the backend's stream slots (a
     CudaBackend unless another backend is given)."""
 
-    def __init__(self, device=0, streams=3, budget_bytes=48 << 30, pool_bytes=1 << 30,
-                 max_batch_bytes=256 << 20, max_batch_requests=8192, replay_cap_bytes=None,
+    def __init__(self, device=0, streams=6, budget_bytes=48 << 30, pool_bytes=1 << 30,
+                 max_batch_bytes=128 << 20, max_batch_requests=8192, replay_cap_bytes=None,
                  seed=0x5E4E, backend=None, policy="small_first", max_adaptive_bytes=None,
                  backlog_batches=4, dense_build=1):
         if policy not in ("fifo", "small_first"):

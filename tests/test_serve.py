@@ -288,7 +288,7 @@ def test_served_workload_verdicts_oracle_and_alone_vs_mix():
     import oracle_mt
     w = serve.Workload(_small_spec())
     capture = serve.capture_sample(w, 8)
-    srv = serve.Server(0, streams=3, budget_bytes=4 << 30, pool_bytes=64 << 20,
+    srv = serve.Server(0, streams=6, budget_bytes=4 << 30, pool_bytes=64 << 20,
                        max_batch_bytes=64 << 20, max_batch_requests=1024)
     try:
         st = srv.run(w, capture=capture, verify_every=1)
