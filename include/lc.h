@@ -268,7 +268,14 @@ lc_status lc_wait_batch_host(lc_ctx* ctx, uint64_t ticket);
  * a smaller batch, whose grid is cut to fewer CTAs per SM, runs the build
  * that keeps it on the FP64 pipe (lc_partial_mask), whose shorter
  * dependency chains suit fewer resident warps (0 = auto: the threads of
- * the full persistent grid).  None of these changes results. */
+ * the full persistent grid).  split_rows: a batch of the FP64-pipe variant
+ * with fewer parts than this runs its split build, in which each part's
+ * three coordinates are computed by three warps of a 96-thread CTA that
+ * exchange them through shared memory every Euler step (a warp issues at
+ * most one binary64 instruction per 64 cycles, so this shortens one part's
+ * latency while the GPU is far from full; 0 = auto: 64 parts per SM with
+ * one Euler step per byte, never with more).  None of these changes
+ * results. */
 typedef struct {
   uint32_t threads_per_cta;
   uint32_t ctas_per_sm;
@@ -277,6 +284,7 @@ typedef struct {
   uint32_t host_chunk_mib;
   uint32_t dense_build;
   uint32_t full_grid_rows;
+  uint32_t split_rows;
 } lc_launch;
 
 lc_status lc_ctx_get_launch(const lc_ctx* ctx, lc_launch* out);

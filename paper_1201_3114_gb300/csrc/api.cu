@@ -117,7 +117,7 @@ struct lc_ctx {
     int cur_grid = 0;  // CTAs the executable graph launches now
   } graphs[kNumVariants];
 
-  lc_launch launch{256, 0, 0, 0, 0, 0, 0};
+  lc_launch launch{256, 0, 0, 0, 0, 0, 0, 0};
   std::vector<lc_tune_entry> tune_report;  // the last lc_tune's candidates
 
   std::unordered_map<std::string, HostKey> keys;
@@ -301,8 +301,10 @@ lc_status build_graph(lc_ctx* ctx, int v) {
   G.exec = nullptr;
   G.graph = nullptr;
   G.valid = false;
-  // the counting variants' shared-memory slots are sized for their own CTA shape
-  const int threads = variant_has_ct_stats(v) ? kCtStatsThreads : (int)ctx->launch.threads_per_cta;
+  // the counting and split variants have CTA shapes of their own
+  const int threads = v == kVariantV1Split       ? kSplitThreads
+                      : variant_has_ct_stats(v) ? kCtStatsThreads
+                                                : (int)ctx->launch.threads_per_cta;
   int per_sm = resident_ctas(v, threads);
   if (ctx->launch.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)ctx->launch.ctas_per_sm);
   G.grid = ctx->sm_count * per_sm;
@@ -376,7 +378,13 @@ int batch_variant(const lc_ctx* ctx, size_t nrows, bool msg_k = false) {
   if (ctx->variant != kVariantV1) return ctx->variant;
   const uint64_t thr = ctx->launch.small_batch_rows ? ctx->launch.small_batch_rows
                                                     : (uint64_t)ctx->sm_count * kSmallBatchRowsPerSm;
-  if (nrows < thr) return kVariantV1Latency;
+  if (nrows < thr) {
+    // auto: one Euler step per byte only (with more, the exchanges outweigh the gain)
+    const uint64_t split = ctx->launch.split_rows ? ctx->launch.split_rows
+                           : ctx->params.steps_per_byte == 1 ? (uint64_t)ctx->sm_count * kSplitBatchRowsPerSm
+                                                             : 0;
+    return nrows < split ? kVariantV1Split : kVariantV1Latency;
+  }
   const int full = ctx->launch.dense_build ? kVariantV1Dense : kVariantV1;
   // a batch that does not fill the persistent grid runs on fewer CTAs per SM
   uint64_t fill = ctx->launch.full_grid_rows;
@@ -561,7 +569,10 @@ lc_status run_batch_impl(lc_ctx* ctx, const lc_req* reqs, size_t count, int32_t*
   const uint64_t threads = variant_has_ct_stats(v) ? (uint64_t)kCtStatsThreads : ctx->launch.threads_per_cta;
   const int full_per_sm = std::max(1, G.grid / std::max(1, ctx->sm_count));
   const uint64_t need = (nrows + (uint64_t)ctx->sm_count * threads - 1) / ((uint64_t)ctx->sm_count * threads);
-  const int grid = ctx->sm_count * (int)std::min<uint64_t>(std::max<uint64_t>(need, 1), (uint64_t)full_per_sm);
+  int grid = ctx->sm_count * (int)std::min<uint64_t>(std::max<uint64_t>(need, 1), (uint64_t)full_per_sm);
+  // the split kernel: one CTA per 32 parts (not persistent)
+  if (v == kVariantV1Split)
+    grid = (int)std::max<uint64_t>(1, (nrows + kSplitRowsPerCta - 1) / kSplitRowsPerCta);
   hdr.rows_per_warp = rows_per_warp(nrows, (uint64_t)grid * (threads / 32));
   uint8_t* w = sg.host;
   memcpy(w, &hdr, sizeof hdr);
@@ -1181,7 +1192,7 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
       if (maxc > 1) cands.push_back((uint32_t)(maxc - 1));
       for (uint32_t c : cands) {
         // small_batch_rows = 1: the probe runs the throughput variant
-        ctx->launch = lc_launch{tpc, c, 0, 1, saved.host_chunk_mib, dense, saved.full_grid_rows};
+        ctx->launch = lc_launch{tpc, c, 0, 1, saved.host_chunk_mib, dense, saved.full_grid_rows, saved.split_rows};
         invalidate_graphs(ctx);
         st = run_batch_impl(ctx, reqs.data(), count, stat, LC_PARALLEL, s);  // graph build, warm-up
         if (st != LC_OK) break;
@@ -1198,7 +1209,8 @@ lc_status lc_tune(lc_ctx* ctx, size_t probe_bytes, void* stream, lc_launch* best
         if (st != LC_OK) break;
         std::sort(ms3.begin(), ms3.end());
         const double med = ms3[1];
-        lc_launch rec{tpc, c, 0, saved.small_batch_rows, saved.host_chunk_mib, dense, saved.full_grid_rows};
+        lc_launch rec{tpc, c, 0, saved.small_batch_rows, saved.host_chunk_mib, dense, saved.full_grid_rows,
+                      saved.split_rows};
         ctx->tune_report.push_back(lc_tune_entry{rec, med});
         if (med < best_ms) {
           best_ms = med;

@@ -331,9 +331,11 @@ struct V1Path {
     if (M & kEmuFloor) return sfp::floor_scaled_lo32(a);
     return sfp::hw_floor13_lo32(a);
   }
+  // the warm-up's own split; the all-FP64 build (M = 0) keeps it on the FP64 pipe too
+  static constexpr uint32_t kWarmMask = M ? (uint32_t)LC_WARM_MASK : 0u;
   __device__ __forceinline__ void warm(const DevParams& p) {
     const double beta = p.beta, dt = p.dt;
-    for (uint32_t s = 0; s < p.n_warm; s++) euler_v1<(uint32_t)LC_WARM_MASK>(x, y, z, beta, dt);
+    for (uint32_t s = 0; s < p.n_warm; s++) euler_v1<kWarmMask>(x, y, z, beta, dt);
   }
   __device__ __forceinline__ void set_alpha() {
     V0 = vf(pick(mu0, x, y, z));
@@ -688,6 +690,230 @@ __global__ void ct_stats_fixup_kernel(const uint8_t* __restrict__ ws, uint32_t b
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split latency kernel, for v1 batches far too small to fill the GPU (every
+// binary64 operation on the FP64 pipe).  A warp issues at most one binary64
+// instruction every 64 cycles, whatever its active lanes, so one part's byte
+// step (~21 binary64 instructions) costs ~1,350 cycles on a single warp.
+// Here lane l of the three warps of a 96-thread CTA holds part
+// 32 * blockIdx.x + l: warp c computes coordinate c of Eq. 1 in every Euler
+// step, and the three new coordinates (and, after the last Euler step of a
+// byte, each one plus its a') are exchanged through shared memory, one
+// barrier per Euler step.  The byte bookkeeping of Steps 1-3, the kick and
+// the alpha scalings run identically in all three warps; warp 0 writes the
+// output and the verdict.  Every barrier is reached by all 96 threads the
+// same number of times: the loops run the CTA's common counts (the warm-up
+// length, the longest part plus the tag), and lanes whose part is shorter, or
+// that hold no part, compute on zeros without writing.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSplitLanes = 32;
+
+// Coordinate c of one forward-Euler step of Eq. 1, each operation rounded
+// once in the order of euler_hw.
+__device__ __forceinline__ double euler_coord(uint32_t c, double x, double y, double z, const DevParams& p) {
+  if (c == 0) return __dadd_rn(x, __dmul_rn(p.dt, __dmul_rn(p.sigma, __dsub_rn(y, x))));
+  if (c == 1) return __dadd_rn(y, __dmul_rn(p.dt, __dsub_rn(__dsub_rn(__dmul_rn(p.rho, x), y), __dmul_rn(x, z))));
+  return __dadd_rn(z, __dmul_rn(p.dt, __dsub_rn(__dmul_rn(x, y), __dmul_rn(p.beta, z))));
+}
+
+// Input byte t of a lane's stream: the part's body, then its tag (the
+// ciphertext's tag bytes when decrypting, LE64(n) when encrypting), then 0.
+__device__ __forceinline__ uint32_t split_in_byte(const uint8_t* src, const uint8_t* tag_in, uint64_t len,
+                                                  uint32_t tag_len, uint64_t n, uint32_t dec, uint64_t t) {
+  if (t < len) return src[t];
+  if (t < len + tag_len) return dec ? tag_in[t - len] : (uint32_t)(n >> (8 * (t - len))) & 255u;
+  return 0u;
+}
+
+__device__ __forceinline__ uint64_t split_load8(const uint8_t* src, const uint8_t* tag_in, uint64_t len,
+                                                uint32_t tag_len, uint64_t n, uint32_t dec, uint64_t t0) {
+  uint64_t v = 0;
+#pragma unroll
+  for (int j = 0; j < 8; j++)
+    v |= (uint64_t)split_in_byte(src, tag_in, len, tag_len, n, dec, t0 + j) << (8 * j);
+  return v;
+}
+
+__global__ void __launch_bounds__(3 * kSplitLanes) split_kernel(const uint8_t* __restrict__ ws,
+                                                                uint32_t* __restrict__ scratch, DevParams p,
+                                                                const double* __restrict__ theta_g,
+                                                                unsigned long long*, unsigned long long*) {
+  __shared__ double s_theta[4 * 256];
+  __shared__ double s_ex[2][3][2][kSplitLanes];  // [buffer][coordinate][new, new + a'][lane]
+  __shared__ uint32_t s_v[2][3][kSplitLanes];     // [buffer][coordinate][lane]: floor(new 10^13), low 32 bits
+  __shared__ unsigned long long s_len;            // the CTA's longest part (bytes)
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_theta[i] = theta_g[i];
+  if (threadIdx.x == 0) s_len = 0ull;
+  __syncthreads();
+
+  const DevHeader* H = reinterpret_cast<const DevHeader*>(ws);
+  const uint32_t nrows = H->nrows;
+  const uint32_t nmsgs = H->nmsgs;
+  const DevMsg* msgs = reinterpret_cast<const DevMsg*>(ws + sizeof(DevHeader));
+  const DevRow* rows = reinterpret_cast<const DevRow*>(msgs + nmsgs);
+  uint32_t* fail = scratch + 4;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t c = threadIdx.x >> 5;  // the coordinate this warp computes
+  const uint32_t r = blockIdx.x * kSplitLanes + lane;
+
+  bool valid = r < nrows;
+  DevRow row{0u, 0u};
+  if (valid) {
+    row = rows[r];
+#ifdef LC_CHECKED
+    if (row.msg >= nmsgs) {
+      if (c == 0) {
+        atomicOr(scratch + 1, 1u);
+        atomicCAS(scratch + 2, 0u, r + 1u);
+      }
+      valid = false;
+    }
+#endif
+  }
+  // the fields of the message this lane needs (zeros for a lane without a part)
+  const DevMsg* gm = msgs + (valid ? row.msg : 0u);
+  const uint32_t flags = valid ? gm->flags : 0u;
+  const uint32_t key_bits = valid ? gm->key_bits : 0u;
+  const uint64_t mn = valid ? gm->n : 0ull;
+  const uint8_t* m_in = valid ? gm->in : nullptr;
+  uint8_t* m_out = valid ? gm->out : nullptr;
+  const bool seq = (flags & kFlagSequential) != 0;
+  const uint32_t dec = (flags & kFlagDecrypt) ? 1u : 0u;
+#ifdef LC_CHECKED
+  if (valid) {
+    const bool in_range = seq ? (row.b == 0) : ((uint64_t)row.b * p.block_len < mn || (mn == 0 && row.b == 0));
+    if (!in_range || (mn && (!m_in || !m_out))) {
+      if (c == 0) {
+        atomicOr(scratch + 1, 2u);
+        atomicCAS(scratch + 2, 0u, r + 1u);
+      }
+      valid = false;
+    }
+  }
+#endif
+  const uint32_t b = row.b;
+  const uint64_t lo = (valid && !seq) ? (uint64_t)b * p.block_len : 0;
+  const uint64_t len = !valid ? 0 : (seq ? mn : min((uint64_t)p.block_len, mn - lo));
+  const uint64_t tag_off = mn + (seq ? 0 : (uint64_t)b * p.tag_len);
+  const uint8_t* src = valid ? m_in + lo : nullptr;
+  const uint8_t* tag_in = valid ? m_in + tag_off : nullptr;
+  uint8_t* dst = valid ? m_out + lo : nullptr;
+  uint8_t* tag_out = valid ? m_out + tag_off : nullptr;
+  const uint32_t tag_len = valid ? p.tag_len : 0u;
+  if (c == 0 && valid) atomicMax(&s_len, (unsigned long long)len);
+  __syncthreads();  // s_len complete before any thread reads it (n_warm may be 0)
+  const uint64_t total = s_len + p.tag_len;  // the CTA's common byte-step count
+
+  // Eq. 5 plus the part offset, then the warm-up
+  const double off = __dmul_rn((double)b, p.eta);
+  double x = valid ? __dadd_rn(gm->base[0], off) : 0.0;
+  double y = valid ? __dadd_rn(gm->base[1], off) : 0.0;
+  double z = valid ? __dadd_rn(gm->base[2], off) : 0.0;
+  const double ap = valid ? gm->aprime[c] : 0.0;  // a' of this warp's coordinate
+  uint32_t buf = 0;
+  for (uint32_t s = 0; s < p.n_warm; s++) {
+    s_ex[buf][c][0][lane] = euler_coord(c, x, y, z, p);
+    __syncthreads();
+    x = s_ex[buf][0][0][lane];
+    y = s_ex[buf][1][0][lane];
+    z = s_ex[buf][2][0][lane];
+    buf ^= 1u;
+  }
+  uint32_t mu0 = key_bits & 3u, mu1 = (key_bits >> 2) & 3u, mu2 = (key_bits >> 4) & 3u;
+  uint32_t om0 = (key_bits >> 8) & 15u, om1 = (key_bits >> 12) & 15u, om2 = (key_bits >> 16) & 15u;
+  using VP = V1Path<0u>;
+  // floor(RN(r_j 10^13)) of all three coordinates (each warp scales its own
+  // one, the three are exchanged); V_i = the one of coordinate mu_i
+  uint32_t Wx, Wy, Wz;
+  {
+    const uint32_t own = VP::vf(c == 0 ? x : (c == 1 ? y : z));
+    s_v[buf][c][lane] = own;
+    __syncthreads();
+    Wx = s_v[buf][0][lane];
+    Wy = s_v[buf][1][lane];
+    Wz = s_v[buf][2][lane];
+    buf ^= 1u;
+  }
+  auto sel = [&](uint32_t m) { return m == 0 ? Wx : (m == 1 ? Wy : Wz); };
+  uint32_t V0 = sel(mu0), V1 = sel(mu1), V2 = sel(mu2);
+
+  uint64_t cur8 = split_load8(src, tag_in, len, tag_len, mn, dec, 0);
+  uint64_t next8 = split_load8(src, tag_in, len, tag_len, mn, dec, 8);
+  bool ok = true;
+  for (uint64_t t = 0; t < total; t++) {
+    if (t && (t & 7u) == 0) {
+      cur8 = next8;
+      next8 = split_load8(src, tag_in, len, tag_len, mn, dec, t + 8);
+    }
+    const uint32_t in = (uint32_t)(cur8 >> (8 * (t & 7u))) & 255u;
+    // Step 1
+    const uint32_t R1 = VP::rb(V0, om0), R2 = VP::rb(V1, om1);
+    const uint32_t sum = R1 + R2;
+    const uint32_t out = (dec ? (in - sum) : (in + sum)) & 255u;
+    const uint32_t P = dec ? out : in;
+    // Step 2: the kick on r[mu_3] (in every warp), then S Euler steps
+    const double kicked = __dadd_rn(pick(mu2, x, y, z), s_theta[om2 * 256u + P]);
+    x = mu2 == 0 ? kicked : x;
+    y = mu2 == 1 ? kicked : y;
+    z = mu2 == 2 ? kicked : z;
+    double xa, ya, za;
+    for (uint32_t k = 1; k < p.steps_per_byte; k++) {
+      s_ex[buf][c][0][lane] = euler_coord(c, x, y, z, p);
+      __syncthreads();
+      x = s_ex[buf][0][0][lane];
+      y = s_ex[buf][1][0][lane];
+      z = s_ex[buf][2][0][lane];
+      buf ^= 1u;
+    }
+    {
+      // the byte's last Euler step, with this coordinate's alpha scaling
+      // (Step 3 reads alpha from r after F) and r + a'
+      const double cn = euler_coord(c, x, y, z, p);
+      s_ex[buf][c][0][lane] = cn;
+      s_v[buf][c][lane] = VP::vf(cn);
+      s_ex[buf][c][1][lane] = __dadd_rn(cn, ap);
+      __syncthreads();
+      x = s_ex[buf][0][0][lane];
+      y = s_ex[buf][1][0][lane];
+      z = s_ex[buf][2][0][lane];
+      xa = s_ex[buf][0][1][lane];
+      ya = s_ex[buf][1][1][lane];
+      za = s_ex[buf][2][1][lane];
+      Wx = s_v[buf][0][lane];
+      Wy = s_v[buf][1][lane];
+      Wz = s_v[buf][2][lane];
+      buf ^= 1u;
+    }
+    // Step 3: mu from the old alpha and Omega; alpha re-read with the new mu;
+    // Omega from the new alpha and the old Omega; r += a' last
+    const uint32_t R3 = VP::rb(V2, om2);
+    mu0 = (mu0 + R1) % 3u;
+    mu1 = (mu1 + R2) % 3u;
+    mu2 = (mu2 + R3) % 3u;
+    V0 = sel(mu0);
+    V1 = sel(mu1);
+    V2 = sel(mu2);
+    om0 = (om0 + VP::rb(V0, om0)) & 3u;
+    om1 = (om1 + VP::rb(V1, om1)) & 3u;
+    om2 = (om2 + VP::rb(V2, om2)) & 3u;
+    x = xa;
+    y = ya;
+    z = za;
+    // Output, after this step's barriers: every warp has read byte t, so an
+    // in-place part stays safe.
+    if (c == 0 && t < len + tag_len) {
+      if (t < len) {
+        dst[t] = (uint8_t)out;
+      } else if (!dec) {
+        tag_out[t - len] = (uint8_t)out;
+      } else {
+        ok = ok && (out == ((uint32_t)(mn >> (8 * (t - len))) & 255u));
+      }
+    }
+  }
+  if (c == 0 && valid && dec && !ok) atomicOr(fail + row.msg, 1u);
+}
+
 // After the batch: per-request status, and fail-closed zeroing of the
 // plaintext of every decryption whose verdict failed.
 __global__ void finalize_kernel(const uint8_t* __restrict__ ws, const uint32_t* __restrict__ scratch,
@@ -770,6 +996,7 @@ int kernel_variant(const DevParams& p) {
 }
 
 size_t batch_kernel_smem(int variant) {
+  if (variant == kVariantV1Split) return 0;  // static shared memory only
   return (variant_is_general(variant) ? kThetaEntries : 4 * 256) * sizeof(double) +
          (variant_has_ct_stats(variant) ? kCtStatsSmem : 0);
 }
@@ -782,6 +1009,7 @@ const void* batch_kernel_ptr(int variant) {
     case kVariantV1Dense: return reinterpret_cast<const void*>(&batch_kernel<KV1Dense>);
     case kVariantV1Partial: return reinterpret_cast<const void*>(&batch_kernel<KV1Partial>);
     case kVariantV1PartialDense: return reinterpret_cast<const void*>(&batch_kernel<KV1PartialDense>);
+    case kVariantV1Split: return reinterpret_cast<const void*>(&split_kernel);
     case kVariantV1Digits: return reinterpret_cast<const void*>(&batch_kernel<KV1, true>);
     case kVariantGeneralDigits: return reinterpret_cast<const void*>(&batch_kernel<KGeneral, true>);
     case kVariantV1CtStats: return reinterpret_cast<const void*>(&batch_kernel<KV1, false, true>);
@@ -816,6 +1044,10 @@ cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, ui
       break;
     case kVariantV1PartialDense:
       batch_kernel<KV1PartialDense><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    case kVariantV1Split:
+      if (block != kSplitThreads) return cudaErrorInvalidValue;
+      split_kernel<<<grid, block, 0, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantV1Digits:
       batch_kernel<KV1, true><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);

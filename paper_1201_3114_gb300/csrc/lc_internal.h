@@ -42,7 +42,15 @@ constexpr int kVariantGeneralDigitsCtStats = 10;
 constexpr int kVariantV1Partial = 11;
 // kVariantV1Partial compiled for 4 resident 256-thread CTAs per SM.
 constexpr int kVariantV1PartialDense = 12;
-constexpr int kNumVariants = 13;
+// The v1 constants, all binary64 work on the FP64 pipe, each part's three
+// coordinates on three warps of a 96-thread CTA (far-from-full batches).
+constexpr int kVariantV1Split = 13;
+constexpr int kNumVariants = 14;
+constexpr int kSplitThreads = 96;
+constexpr uint32_t kSplitRowsPerCta = 32;
+// Below this many parts per SM a v1 batch of the FP64-pipe variant runs split
+// (measured crossover on GB300).
+constexpr uint32_t kSplitBatchRowsPerSm = 64;
 
 inline bool variant_has_ct_stats(int v) { return v >= kVariantV1CtStats && v <= kVariantGeneralDigitsCtStats; }
 inline bool variant_is_general(int v) {

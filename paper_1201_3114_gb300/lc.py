@@ -79,6 +79,7 @@ class lc_launch(C.Structure):
         ("host_chunk_mib", C.c_uint32),
         ("dense_build", C.c_uint32),
         ("full_grid_rows", C.c_uint32),
+        ("split_rows", C.c_uint32),
     ]
 
     def as_dict(self):
@@ -493,9 +494,10 @@ def lc_ctx_get_launch(ctx) -> lc_launch:
 
 
 def lc_ctx_set_launch(ctx, threads_per_cta=256, ctas_per_sm=0, smem_staging=0,
-                      small_batch_rows=0, host_chunk_mib=0, dense_build=0, full_grid_rows=0) -> int:
+                      small_batch_rows=0, host_chunk_mib=0, dense_build=0, full_grid_rows=0,
+                      split_rows=0) -> int:
     l = lc_launch(threads_per_cta, ctas_per_sm, smem_staging, small_batch_rows, host_chunk_mib,
-                  dense_build, full_grid_rows)
+                  dense_build, full_grid_rows, split_rows)
     return load().lc_ctx_set_launch(ctx, C.byref(l))
 
 

@@ -151,17 +151,28 @@ def test_every_alignment_pair(ctx, mode):
         assert (got[:pout] == 0x5A).all() and (got[pout + y.size:] == 0x5A).all(), i
 
 
-def test_in_place(ctx):
+@pytest.mark.parametrize("shape", [(256, 0, 0, 0), (256, 0, 0, 0, 0, 0, 0, 1), (256, 0, 0, 1)],
+                         ids=["three-warps", "fp64-only", "int-split"])
+def test_in_place(ctx, shape):
+    # every build reads each byte before it is written
     n = 3 * B + 9
     P = synth.uniform_bytes(45, n)
     pw = b"in-place"
     want = O.encrypt(pw, P)
     buf = torch.zeros(want.size, dtype=torch.uint8, device="cuda")
     buf[:n] = dev(P)
-    assert lc.lc_encrypt(ctx.handle, pw, buf, n, buf, want.size, lc.LC_PARALLEL) == lc.LC_OK
-    assert np.array_equal(host(buf), want)
-    assert lc.lc_decrypt(ctx.handle, pw, buf, want.size, buf, n, lc.LC_PARALLEL) == lc.LC_OK
-    assert np.array_equal(host(buf)[:n], P)
+    try:
+        assert lc.lc_ctx_set_launch(ctx.handle, *shape) == lc.LC_OK
+        for mode in (lc.LC_PARALLEL, lc.LC_SEQUENTIAL):
+            want = O.encrypt(pw, P, mode)
+            buf = torch.zeros(want.size, dtype=torch.uint8, device="cuda")
+            buf[:n] = dev(P)
+            assert lc.lc_encrypt(ctx.handle, pw, buf, n, buf, want.size, mode) == lc.LC_OK
+            assert np.array_equal(host(buf), want), mode
+            assert lc.lc_decrypt(ctx.handle, pw, buf, want.size, buf, n, mode) == lc.LC_OK
+            assert np.array_equal(host(buf)[:n], P), mode
+    finally:
+        lc.lc_ctx_set_launch(ctx.handle, 256, 0)
 
 
 def test_config2_text_both_modes_and_tamper(ctx):
@@ -365,9 +376,10 @@ def test_launch_shapes_do_not_change_results(ctx):
         for tpc, cps in ((32, 1), (64, 0), (128, 2), (256, 0), (256, 4)):
             # integer-split variant (full-grid and partial-grid builds, each
             # default and dense), FP64-only variant
-            for small, dense, full in ((1, 0, 1), (1, 1, 1), (1, 0, 0), (1, 1, 0), (0xFFFFFFFF, 0, 0)):
-                assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small, 0, dense, full) == lc.LC_OK
-                assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small, dense, full)
+            for small, dense, full, split in ((1, 0, 1, 0), (1, 1, 1, 0), (1, 0, 0, 0), (1, 1, 0, 0),
+                                              (0xFFFFFFFF, 0, 0, 1), (0xFFFFFFFF, 0, 0, 0xFFFFFFFF)):
+                assert lc.lc_ctx_set_launch(ctx.handle, tpc, cps, 0, small, 0, dense, full, split) == lc.LC_OK
+                assert np.array_equal(gpu_encrypt(ctx, pw, P), want), (tpc, cps, small, dense, full, split)
         assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 1, 0) == lc.LC_ERR_ARG
         assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, 0, 0, 2) == lc.LC_ERR_ARG
         best = lc.lc_tune(ctx.handle, 8 << 20)
@@ -383,14 +395,17 @@ def test_launch_shapes_do_not_change_results(ctx):
         lc.lc_ctx_set_launch(ctx.handle, 256, 0)
 
 
-@pytest.mark.parametrize("small,full", [(1, 1), (1, 0), (0xFFFFFFFF, 0)],
-                         ids=["int-split-full-grid", "int-split-partial-grid", "fp64-only"])
-def test_both_v1_kernel_variants(ctx, small, full):
-    # The batched kernel has three v1 builds: binary64 multiplies (and, on a
-    # full grid, the kick) on the integer pipes, or everything on the FP64
-    # pipe; force each one.
+@pytest.mark.parametrize("small,full,split", [(1, 1, 0), (1, 0, 0), (0xFFFFFFFF, 0, 1),
+                                              (0xFFFFFFFF, 0, 0xFFFFFFFF)],
+                         ids=["int-split-full-grid", "int-split-partial-grid", "fp64-only",
+                              "fp64-three-warps"])
+def test_both_v1_kernel_variants(ctx, small, full, split):
+    # The batched kernel has four v1 builds: binary64 multiplies (and, on a
+    # full grid, the kick) on the integer pipes; everything on the FP64 pipe,
+    # one part per thread or each part's coordinates on three warps; force
+    # each one.
     try:
-        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, small, 0, 0, full) == lc.LC_OK
+        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, small, 0, 0, full, split) == lc.LC_OK
         for i, n in enumerate([0, 1, 17, B - 1, B + 1, 5 * B + 3]):
             for mode in (lc.LC_PARALLEL, lc.LC_SEQUENTIAL):
                 pw = synth.password(synth.subseed(60, i), 2 + 5 * i)
