@@ -663,6 +663,35 @@ def profile_case(args):
     return 0
 
 
+def latency_case(args):
+    """One parallel-mode encryption of args.latency_case KiB per step with the
+    FP64-pipe variant: the split build (each part's coordinates on three
+    warps, the default for small batches) and the one-part-per-thread build."""
+    import torch
+    from paper_1201_3114_gb300 import lc, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.latency_case << 10
+    P = torch.from_numpy(synth.uniform_bytes(synth.config_seed(1) + 30, n)).cuda()
+    out = {"case": "latency", "kib": args.latency_case, "parts": -(-n // 4096), "source_hash": source_hash()}
+    with lc.Context(0) as ctx:
+        for name, split in (("three_warps", 0xFFFFFFFF), ("one_thread", 1)):
+            lc.check(lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, 0xFFFFFFFF, 0, 0, 0, split))
+            enc = lambda: ctx.encrypt(b"latency-case-password", P, stream=stream)
+            for _ in range(args.warmup):
+                enc()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                enc()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name + "_ms"] = e0.elapsed_time(e1) / args.steps
+    print(json.dumps(out))
+    return 0
+
+
 def next_rows(args):
     """Throughput of the widened rows: batched sequential mode (one message
     per thread), the S = 3000 steps-per-byte profile, the delta t = 0.027
@@ -816,6 +845,8 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0, metavar="MIB",
                     help="only time one MIB-MiB parallel-mode encryption per step (a small "
                          "case for ncu captures); prints a short JSON line")
+    ap.add_argument("--latency-case", type=int, default=0, metavar="KIB",
+                    help="time one small message with both FP64-pipe builds (one JSON line)")
     ap.add_argument("--next-rows", action="store_true",
                     help="only time the widened rows (batched sequential mode, the S = 3000 "
                          "and delta t = 0.027 profiles, the statistics kernel); one JSON line")
@@ -826,6 +857,8 @@ def main():
         return reference_arm(args)
     if args.profile_case:
         return profile_case(args)
+    if args.latency_case:
+        return latency_case(args)
     if args.next_rows:
         return next_rows(args)
 
