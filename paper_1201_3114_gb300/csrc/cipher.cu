@@ -29,15 +29,19 @@
 #endif
 // The same for the warm-up steps before the first byte (they carry no
 // per-byte bookkeeping, so their best split can differ): the eight
-// multiplies.
+// multiplies and the z update.
 #ifndef LC_WARM_MASK
-#define LC_WARM_MASK 0xFFu
+#define LC_WARM_MASK 0x40FFu
 #endif
 // The byte steps of batches that leave the persistent grid partly empty:
 // the eight multiplies and the alpha scaling (the emulated kick lengthens
 // each byte's chain, which fewer resident warps cannot hide).
 #ifndef LC_PARTIAL_MASK
 #define LC_PARTIAL_MASK 0xFFu
+#endif
+// and their warm-up steps
+#ifndef LC_PARTIAL_WARM_MASK
+#define LC_PARTIAL_WARM_MASK 0xFFu
 #endif
 // Minimum resident 256-thread CTAs per SM the v1 kernel is compiled for
 // (bounds its registers per thread).  Chosen by measurement on GB300.
@@ -107,6 +111,21 @@ __device__ __forceinline__ void euler_hw(double& x, double& y, double& z, const 
 
 // The same step with sigma = 10 = 5 * 2 and rho = 28 = 7 * 4, each
 // operation on the pipe the mask M selects.
+// dt * v and beta * v in the v1 builds, which run only with dt = 0.01 and
+// beta = RN(8/3): on the integer pipe those values are compile-time
+// constants of the multiply (bit patterns below); on the FP64 pipe the
+// parameters are used as passed.
+constexpr uint64_t kV1DtBits = 0x3F847AE147AE147Bull;    // 0.01
+constexpr uint64_t kV1BetaBits = 0x4005555555555555ull;  // RN(8/3)
+template <bool SW>
+__device__ __forceinline__ double mul_dt(double dt, double v) {
+  return SW ? sfp::dmul_const<kV1DtBits>(v) : __dmul_rn(dt, v);
+}
+template <bool SW>
+__device__ __forceinline__ double mul_beta(double beta, double v) {
+  return SW ? sfp::dmul_const<kV1BetaBits>(v) : __dmul_rn(beta, v);
+}
+
 template <uint32_t M>
 __device__ __forceinline__ void euler_v1(double& x, double& y, double& z, double beta, double dt) {
   const double yx = f_sub<(M & kEmuSubYX) != 0>(y, x);
@@ -115,11 +134,11 @@ __device__ __forceinline__ void euler_v1(double& x, double& y, double& z, double
   const double xz = f_mul<(M & kEmuMulXZ) != 0>(x, z);
   const double dy = f_sub<(M & kEmuSubXZ) != 0>(f_sub<(M & kEmuSubRY) != 0>(rx, y), xz);
   const double xy = f_mul<(M & kEmuMulXY) != 0>(x, y);
-  const double bz = f_mul<(M & kEmuMulBZ) != 0>(beta, z);
+  const double bz = mul_beta<(M & kEmuMulBZ) != 0>(beta, z);
   const double dz = f_sub<(M & kEmuSubBZ) != 0>(xy, bz);
-  x = f_add<(M & kEmuAddX) != 0>(x, f_mul<(M & kEmuMulDtX) != 0>(dt, dx));
-  y = f_add<(M & kEmuAddY) != 0>(y, f_mul<(M & kEmuMulDtY) != 0>(dt, dy));
-  z = f_add<(M & kEmuAddZ) != 0>(z, f_mul<(M & kEmuMulDtZ) != 0>(dt, dz));
+  x = f_add<(M & kEmuAddX) != 0>(x, mul_dt<(M & kEmuMulDtX) != 0>(dt, dx));
+  y = f_add<(M & kEmuAddY) != 0>(y, mul_dt<(M & kEmuMulDtY) != 0>(dt, dy));
+  z = f_add<(M & kEmuAddZ) != 0>(z, mul_dt<(M & kEmuMulDtZ) != 0>(dt, dz));
 }
 
 // floor(RN(alpha * 10^13)) as a two's complement int64: cvt.rmi.s64.f64
@@ -312,7 +331,7 @@ struct GeneralPath {
 // and alpha_j are the same coordinate and V_i = V_j is computed once; after
 // the (mu, Omega) lock that every part reaches within a few dozen bytes this
 // is one conversion per byte instead of three.
-template <uint32_t M, int MinCtas = LC_MIN_CTAS>
+template <uint32_t M, int MinCtas = LC_MIN_CTAS, uint32_t WM = (M ? (uint32_t)LC_WARM_MASK : 0u)>
 struct V1Path {
   double x, y, z, ax, ay, az;
   uint32_t V0, V1, V2;
@@ -331,11 +350,11 @@ struct V1Path {
     if (M & kEmuFloor) return sfp::floor_scaled_lo32(a);
     return sfp::hw_floor13_lo32(a);
   }
-  // the warm-up's own split; the all-FP64 build (M = 0) keeps it on the FP64 pipe too
-  static constexpr uint32_t kWarmMask = M ? (uint32_t)LC_WARM_MASK : 0u;
+  // the warm-up's own split WM; the all-FP64 build (M = 0) keeps it on the
+  // FP64 pipe too
   __device__ __forceinline__ void warm(const DevParams& p) {
     const double beta = p.beta, dt = p.dt;
-    for (uint32_t s = 0; s < p.n_warm; s++) euler_v1<kWarmMask>(x, y, z, beta, dt);
+    for (uint32_t s = 0; s < p.n_warm; s++) euler_v1<WM>(x, y, z, beta, dt);
   }
   __device__ __forceinline__ void set_alpha() {
     V0 = vf(pick(mu0, x, y, z));
@@ -980,8 +999,8 @@ using KV1Lat = V1Path<0u>;
 // The throughput variant compiled for 4 resident 256-thread CTAs per SM (at
 // most 64 registers per thread): one of the autotuner's candidates.
 using KV1Dense = V1Path<LC_EMU_MASK, 4>;
-using KV1Partial = V1Path<LC_PARTIAL_MASK>;
-using KV1PartialDense = V1Path<LC_PARTIAL_MASK, 4>;
+using KV1Partial = V1Path<LC_PARTIAL_MASK, LC_MIN_CTAS, LC_PARTIAL_WARM_MASK>;
+using KV1PartialDense = V1Path<LC_PARTIAL_MASK, 4, LC_PARTIAL_WARM_MASK>;
 
 }  // namespace
 
@@ -991,7 +1010,9 @@ using KV1PartialDense = V1Path<LC_PARTIAL_MASK, 4>;
 
 int kernel_variant(const DevParams& p) {
   if (!p.k_all4 || p.omega_alpha_shift) return kVariantGeneral;
-  if (p.sigma == 10.0 && p.rho == 28.0) return kVariantV1;
+  // the v1 builds take sigma = 10 and rho = 28 as small-integer multiples
+  // and dt = 0.01, beta = RN(8/3) as compile-time constants
+  if (p.sigma == 10.0 && p.rho == 28.0 && p.dt == 0.01 && p.beta == 8.0 / 3.0) return kVariantV1;
   return kVariantGeneral4;
 }
 

@@ -117,13 +117,13 @@ __device__ __forceinline__ uint32_t floor_scaled_lo32(double a) {
   return ip;
 }
 
-// RN(a * b) for two normal operands with a normal result.
-__device__ __forceinline__ double dmul(double a, double b) {
-  const uint32_t xl = lo32(a), xh = hi32(a), yl = lo32(b), yh = hi32(b);
-  const uint32_t ea = (xh >> 20) & 0x7FFu, eb = (yh >> 20) & 0x7FFu;
-  const uint32_t er = ea + eb - 1023u;  // biased exponent if the product stays in [1, 2)
-  if (ea - 1u >= 2046u || eb - 1u >= 2046u || er - 1u >= 2044u) return hw_mul(a, b);
-  const uint32_t a1 = (xh & 0xFFFFFu) | 0x100000u, b1 = (yh & 0xFFFFFu) | 0x100000u;
+// The integer path of RN(a * b), from the operands' fields: a's low and high
+// words, b's low word, b's significand above bit 32 with its hidden bit, the
+// product's biased exponent if it stays in [1, 2), and the product's sign
+// bit.  The caller has checked that a, b and the result are normal.
+__device__ __forceinline__ double dmul_fields(uint32_t xl, uint32_t xh, uint32_t yl, uint32_t b1, uint32_t er,
+                                              uint32_t sign) {
+  const uint32_t a1 = (xh & 0xFFFFFu) | 0x100000u;
   const uint64_t p00 = (uint64_t)xl * yl;
   const uint64_t mid = (uint64_t)xl * b1 + (uint64_t)a1 * yl;  // < 2^54
   const uint64_t p11 = (uint64_t)a1 * b1;                      // < 2^42
@@ -141,8 +141,32 @@ __device__ __forceinline__ double dmul(double a, double b) {
   const uint32_t up = guard & ((sticky != 0u) | (q0 & 1u));
   q0 += up;
   q1 += (q0 < up) ? 1u : 0u;
-  const uint32_t hi = ((xh ^ yh) & 0x80000000u) + ((er + top - 1u) << 20) + q1;
+  const uint32_t hi = sign + ((er + top - 1u) << 20) + q1;
   return pack(hi, q0);
+}
+
+// RN(a * b) for two normal operands with a normal result.
+__device__ __forceinline__ double dmul(double a, double b) {
+  const uint32_t xl = lo32(a), xh = hi32(a), yl = lo32(b), yh = hi32(b);
+  const uint32_t ea = (xh >> 20) & 0x7FFu, eb = (yh >> 20) & 0x7FFu;
+  const uint32_t er = ea + eb - 1023u;  // biased exponent if the product stays in [1, 2)
+  if (ea - 1u >= 2046u || eb - 1u >= 2046u || er - 1u >= 2044u) return hw_mul(a, b);
+  return dmul_fields(xl, xh, yl, (yh & 0xFFFFFu) | 0x100000u, er, (xh ^ yh) & 0x80000000u);
+}
+
+// RN(a * C) for a compile-time constant C given by its bit pattern CB (a
+// positive normal number): dmul with the constant's fields folded in.
+template <uint64_t CB>
+__device__ __forceinline__ double dmul_const(double a) {
+  constexpr uint32_t yl = (uint32_t)CB;
+  constexpr uint32_t b1 = (uint32_t)((CB >> 32) & 0xFFFFFull) | 0x100000u;
+  constexpr uint32_t eb = (uint32_t)(CB >> 52) & 0x7FFu;
+  static_assert(eb >= 1u && eb <= 2046u && (CB >> 63) == 0, "a positive normal constant");
+  const uint32_t xl = lo32(a), xh = hi32(a);
+  const uint32_t ea = (xh >> 20) & 0x7FFu;
+  const uint32_t er = ea + eb - 1023u;
+  if (ea - 1u >= 2046u || er - 1u >= 2044u) return hw_mul(a, from_bits(CB));
+  return dmul_fields(xl, xh, yl, b1, er, xh & 0x80000000u);
 }
 
 // RN(a + b) for two normal operands (either sign) with a normal result.

@@ -26,6 +26,14 @@ __global__ void eval_kernel(uint32_t op, const uint64_t* __restrict__ a, const u
         s = S::floor_scaled_lo32(x);
         h = (uint32_t)(uint64_t)__double2ll_rd(__dmul_rn(x, 1e13));
         break;
+      case LC_SFP_MULDT:
+        s = S::bits(S::dmul_const<0x3F847AE147AE147Bull>(x));
+        h = S::bits(__dmul_rn(x, 0.01));
+        break;
+      case LC_SFP_MULBETA:
+        s = S::bits(S::dmul_const<0x4005555555555555ull>(x));
+        h = S::bits(__dmul_rn(x, 8.0 / 3.0));
+        break;
       default: break;
     }
     sw[i] = s;
@@ -37,7 +45,7 @@ __global__ void eval_kernel(uint32_t op, const uint64_t* __restrict__ a, const u
 
 extern "C" lc_status lc_softfp_eval(uint32_t op, const uint64_t* a_dev, const uint64_t* b_dev,
                                     uint64_t* sw_dev, uint64_t* hw_dev, size_t n, void* stream) {
-  if (op > LC_SFP_FLOOR13) return LC_ERR_ARG;
+  if (op > LC_SFP_MULBETA) return LC_ERR_ARG;
   if (n && (!a_dev || !sw_dev || !hw_dev)) return LC_ERR_ARG;
   if (n && !b_dev && op <= LC_SFP_MUL) return LC_ERR_ARG;
   if (n == 0) return LC_OK;

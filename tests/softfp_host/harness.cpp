@@ -1,8 +1,9 @@
 // harness.cpp -- checks the integer-path binary64 routines of
 // csrc/softfp64.cuh, compiled for the host, against the host's IEEE-754
 // arithmetic: round to nearest, ties to even (IEEE 754-2019 Sec. 4.3.1) for
-// a + b, a - b, a * b, 10 a and 28 a, and floor(RN(a * 10^13)) converted to
-// int64 with saturation (low 32 bits) for the scaled floor.
+// a + b, a - b, a * b, 10 a, 28 a, 0.01 a and RN(8/3) a (the multiplies by
+// a compile-time constant), and floor(RN(a * 10^13)) converted to int64 with
+// saturation (low 32 bits) for the scaled floor.
 //
 // Operands come from generated classes (a full grid of exponent pairs,
 // the cipher's value range, every adder gap with tie and sticky bit
@@ -33,8 +34,14 @@ namespace S = lc::sfp;
 
 namespace {
 
-enum Op { ADD, SUB, MUL, MUL10, MUL28, FLOOR13, NOPS };
-const char* const kOpName[NOPS] = {"add", "sub", "mul", "mul10", "mul28", "floor13"};
+enum Op { ADD, SUB, MUL, MUL10, MUL28, FLOOR13, MULDT, MULBETA, NOPS };
+const char* const kOpName[NOPS] = {"add", "sub", "mul", "mul10", "mul28", "floor13", "muldt", "mulbeta"};
+
+// the constants of the constant-operand multiplies and their bit patterns
+constexpr double kDt = 0.01;
+constexpr double kBeta = 8.0 / 3.0;
+constexpr uint64_t kDtBits = 0x3F847AE147AE147Bull;
+constexpr uint64_t kBetaBits = 0x4005555555555555ull;
 
 constexpr uint64_t kFrac = 0x000FFFFFFFFFFFFFull;
 
@@ -118,6 +125,8 @@ uint64_t ref(Op op, double a, double b) {
     case MUL10: return to_bits(10.0 * a);
     case MUL28: return to_bits(28.0 * a);
     case FLOOR13: return ref_floor13(a);
+    case MULDT: return to_bits(a * kDt);
+    case MULBETA: return to_bits(a * kBeta);
     default: return 0;
   }
 }
@@ -130,6 +139,8 @@ uint64_t soft(Op op, double a, double b) {
     case MUL10: return S::bits(S::mul_small<5, 1>(a));
     case MUL28: return S::bits(S::mul_small<7, 2>(a));
     case FLOOR13: return S::floor_scaled_lo32(a);
+    case MULDT: return S::bits(S::dmul_const<kDtBits>(a));
+    case MULBETA: return S::bits(S::dmul_const<kBetaBits>(a));
     default: return 0;
   }
 }
@@ -154,6 +165,8 @@ bool is_tie(Op op, double a, double b) {
     case MUL10: r = 10.0 * a; e = fma(10.0, a, -r); break;
     case MUL28: r = 28.0 * a; e = fma(28.0, a, -r); break;
     case FLOOR13: r = a * 1e13; e = fma(a, 1e13, -r); break;
+    case MULDT: r = a * kDt; e = fma(a, kDt, -r); break;
+    case MULBETA: r = a * kBeta; e = fma(a, kBeta, -r); break;
     default: return false;
   }
   if (!isfinite(r) || !isfinite(e) || r == 0.0 || e == 0.0 || fabs(r) < 0x1p-1020) return false;
@@ -188,6 +201,23 @@ double floor_tie(Gen& g) {
   }
 }
 
+// operands a whose product with the constant (bits cb) lies exactly halfway
+// between two binary64 values: with the constant's significand C odd, the
+// product M C drops 52 bits, so M = 2^52 + (2^51 C^-1 mod 2^52), checked to
+// give a 105-bit product, at a random exponent and sign.
+double const_tie(Gen& g, uint64_t cb) {
+  const uint64_t C = (cb & kFrac) | (1ull << 52);
+  uint64_t inv = C;  // inverse of C modulo 2^64 (Newton iteration)
+  for (int k = 0; k < 6; k++) inv *= 2 - C * inv;
+  const uint64_t mask = (1ull << 52) - 1;
+  const uint64_t M = (1ull << 52) | (((inv & mask) << 51) & mask);
+  const unsigned __int128 P = (unsigned __int128)M * C;
+  int bl = 0;
+  for (unsigned __int128 t = P; t; t >>= 1) bl++;
+  if (bl != 105) return 1.0;  // no tie significand for this constant: counted as an ordinary case
+  return g.sign() * ldexp((double)M, g.range(-1000, 1000) - 52);
+}
+
 struct ClassDef {
   const char* name;
   uint64_t base;  // cases at scale 1
@@ -205,12 +235,25 @@ std::vector<ClassDef> classes(Op op) {
   if (op == FLOOR13)
     return {{"exp_grid", 2048ull * 2 * 512}, {"cipher", 4u << 20}, {"wide", 1u << 20}, {"few_bits", 1u << 20},
             {"ties", 1u << 18},               {"exact_int", 1u << 20}, {"small", 1u << 20}};
+  if (op == MULDT || op == MULBETA)
+    return {{"exp_grid", 2048ull * 2 * 512}, {"cipher", 4u << 20}, {"wide", 1u << 20}, {"few_bits", 1u << 20},
+            {"ties", 1u << 18}, {"result_edge", 1u << 20}};
   return {{"exp_grid", 2048ull * 2 * 512}, {"cipher", 4u << 20}, {"wide", 1u << 20}, {"few_bits", 1u << 20}};
 }
 
 void gen(Op op, const char* cls, uint64_t i, Gen& g, double* a, double* b) {
   const bool two = op == ADD || op == SUB || op == MUL;
   *b = 0.0;
+  if ((op == MULDT || op == MULBETA) && !strcmp(cls, "ties")) {
+    *a = const_tie(g, op == MULDT ? kDtBits : kBetaBits);
+    return;
+  }
+  if ((op == MULDT || op == MULBETA) && !strcmp(cls, "result_edge")) {
+    // operands whose product lands next to the normal range's ends
+    const int e = g.below(2) ? g.range(-1030, -1010) : g.range(1015, 1030);
+    *a = g.sign() * ldexp(1.0 + g.unit(), e);
+    return;
+  }
   if (!strcmp(cls, "exp_grid")) {
     if (two) {
       *a = make(g.u64(), (uint32_t)(i % 2048), frac_pattern(g));

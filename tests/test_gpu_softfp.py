@@ -109,13 +109,29 @@ def test_adder_every_exponent_gap_and_cancellation(rng):
     _check(lc.LC_SFP_ADD, _f64(t), _f64(h))
 
 
+def _const_ties(rng, n, c):
+    """a whose product with the constant c lies exactly halfway between two
+    binary64 values: with c's significand C odd, M = 2^52 + (2^51 C^-1 mod
+    2^52) gives a 105-bit M C whose low 52 bits are 2^51."""
+    C = (int(np.float64(c).view(np.uint64)) & ((1 << 52) - 1)) | 1 << 52
+    M = (1 << 52) | ((pow(C, -1, 1 << 52) << 51) % (1 << 52))
+    assert (M * C).bit_length() == 105 and (M * C) % (1 << 52) == 1 << 51
+    e = rng.integers(-1000, 1000, n)
+    return np.ldexp(float(M), e - 52) * rng.choice([-1.0, 1.0], n)
+
+
 def test_small_constant_multiples(rng):
     a = _operands(rng, N)
-    _check(lc.LC_SFP_MUL10, a)
-    _check(lc.LC_SFP_MUL28, a)
     s = _f64(_specials())
-    _check(lc.LC_SFP_MUL10, s)
-    _check(lc.LC_SFP_MUL28, s)
+    for op in (lc.LC_SFP_MUL10, lc.LC_SFP_MUL28, lc.LC_SFP_MULDT, lc.LC_SFP_MULBETA):
+        _check(op, a)
+        _check(op, s)
+    # halfway products and results next to the normal range's ends
+    _check(lc.LC_SFP_MULDT, _f64(_const_ties(rng, 1 << 16, 0.01)))
+    _check(lc.LC_SFP_MULBETA, _f64(_const_ties(rng, 1 << 16, 8.0 / 3.0)))
+    edge = np.ldexp(rng.uniform(1, 2, 1 << 18), rng.choice(np.r_[-1030:-1010, 1015:1031], 1 << 18))
+    _check(lc.LC_SFP_MULDT, _f64(edge))
+    _check(lc.LC_SFP_MULBETA, _f64(edge))
 
 
 def test_general_multiply_ties(rng):

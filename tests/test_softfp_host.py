@@ -12,7 +12,8 @@ reference is the definition of the operation, round to nearest with ties to
 even (IEEE 754-2019 Sec. 4.3.1), as the host's floating-point unit computes
 it.  Mutated copies of the header (a dropped sticky bit, round-half-up,
 truncation in place of floor) must fail, so the classes are shown to reach
-the rounding logic they are meant to test."""
+the rounding logic they are meant to test.  The multiplies by the compile-time
+constants 0.01 and RN(8/3) (dmul_const) run beside the general multiply."""
 import os
 import shutil
 import subprocess
@@ -57,7 +58,7 @@ def test_routines_match_ieee_round_to_nearest_even(harness):
     rc, rows = _run(harness, SCALE)
     bad = {k: v for k, v in rows.items() if v["bad"]}
     assert rc == 0 and not bad, bad
-    ops = {"add", "sub", "mul", "mul10", "mul28", "floor13"}
+    ops = {"add", "sub", "mul", "mul10", "mul28", "floor13", "muldt", "mulbeta"}
     assert {k[0] for k in rows} == ops
     for op in ops:
         cases = sum(v["cases"] for k, v in rows.items() if k[0] == op)
@@ -75,8 +76,12 @@ def test_routines_match_ieee_round_to_nearest_even(harness):
     r = rows[("floor13", "ties")]
     assert r["fast"] == r["cases"] == r["ties"], r
     # the cipher's own value range stays on the integer path
-    for op in ("mul", "mul10", "mul28"):
+    for op in ("mul", "mul10", "mul28", "muldt", "mulbeta"):
         assert rows[(op, "cipher")]["fast"] == rows[(op, "cipher")]["cases"]
+    # every constructed halfway product of the constant multiplies is one
+    for op in ("muldt", "mulbeta"):
+        r = rows[(op, "ties")]
+        assert r["fast"] == r["cases"] == r["ties"], r
     assert rows[("add", "cipher")]["fast"] > 0.9 * rows[("add", "cipher")]["cases"]
 
 
@@ -84,6 +89,10 @@ MUTATIONS = [
     # (what is planted, text replaced, replacement, an (op, class) that must fail)
     ("dmul rounds half up", "const uint32_t up = guard & ((sticky != 0u) | (q0 & 1u));",
      "const uint32_t up = guard;", ("mul", "cipher_consts")),
+    ("the constant multiply rounds half up", "const uint32_t up = guard & ((sticky != 0u) | (q0 & 1u));",
+     "const uint32_t up = guard;", ("muldt", "ties")),
+    ("the constant multiply takes a wrong constant", "return dmul_fields(xl, xh, yl, b1, er, xh & 0x80000000u);",
+     "return dmul_fields(xl, xh, yl ^ 1u, b1, er, xh & 0x80000000u);", ("mulbeta", "cipher")),
     ("dadd rounds half down", "const uint64_t T = R + ((1u << (rp - 1u)) - 1u + last);",
      "const uint64_t T = R + ((1u << (rp - 1u)) - 1u);", ("add", "ties")),
     ("dadd drops the sticky bit", "(s0 | (lost != 0u ? 1u : 0u)) ^ m", "s0 ^ m", ("sub", "gap")),
