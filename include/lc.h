@@ -50,7 +50,8 @@ typedef enum {
                            or an output buffer that is too small */
   LC_ERR_INTEGRITY = 4, /* decryption: a part's tag did not verify */
   LC_ERR_CUDA = 5,      /* CUDA runtime error or no device */
-  LC_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  LC_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up (reserved: no call
+                           of this version waits on the device) */
   LC_ERR_NOMEM = 7      /* device workspace could not be allocated */
 } lc_status;
 
@@ -444,9 +445,7 @@ uint32_t lc_warm_mask(void);
  * S = -sum p_i log2 p_i follows from it) and the sums behind the
  * auto-correlation of Fig. 3, all exact integers: sum x_i, sum x_i^2 and,
  * for k = 1..max_lag (max_lag <= LC_STATS_MAX_LAG), sum_{i < n-k} x_i x_{i+k}.
- * Uses the context's workspace; synchronises `stream`.  LC_ERR_TIMEOUT if a
- * bounded wait of the kernel on its own asynchronous copies gave up (the
- * results are then not valid). */
+ * Uses the context's workspace; synchronises `stream`. */
 #define LC_STATS_MAX_LAG 8
 typedef struct {
   uint64_t n;

@@ -1275,7 +1275,6 @@ lc_status lc_byte_stats(lc_ctx* ctx, const uint8_t* data_dev, size_t n, uint32_t
   LC_CUDA(cudaMemcpyAsync(acc, ctx->stats_dev, sizeof acc, cudaMemcpyDeviceToHost, s));
   LC_CUDA(cudaStreamSynchronize(s));
   ctx->launches += 1;
-  if (acc[256]) return LC_ERR_TIMEOUT;  // a bounded wait of the kernel gave up
   out->n = n;
   // the sums follow exactly from the histogram: sum b * count, sum b^2 * count
   out->sum = 0;

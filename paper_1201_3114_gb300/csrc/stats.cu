@@ -5,26 +5,19 @@
 // the result does not depend on the order in which threads add.
 //
 // One pass over the data, bound by HBM bandwidth in principle and, on
-// GB300, by the shared-memory atomics of the histogram (one per byte) and
-// the integer work of the lagged products.  Each CTA keeps a private
-// histogram in shared memory laid out as [bin][lane]: lane l of every warp
-// counts into column l, so the 32 atomics of a warp instruction always fall
-// in 32 different banks.  Two kernels, each the faster one for its case on
-// GB300:
-//   - histogram only (max_lag = 0): each thread reads 32-byte chunks
-//     straight from global memory with 16-byte loads, the next chunk's loads
-//     issued before the current chunk is counted;
-//   - with lagged products: the bytes reach the CTA as 16 KiB tiles that one
-//     thread copies from global to shared memory with bulk asynchronous
-//     copies (cp.async.bulk, completion on an mbarrier), two tiles in flight
-//     per CTA.  Each thread counts two 32-byte chunks of a tile (plus the
-//     next 8 bytes for the lagged products), forming the sums of products
-//     four bytes at a time with the unsigned 4-way byte dot product
-//     (__dp4a); the partial sums reach the global 64-bit totals once per CTA
-//     at the end.
-// The ragged end of the buffer is read with guarded loads.  The sum and the
-// sum of squares are not accumulated here: they follow exactly from the
-// histogram (the host forms them).
+// GB300, by the shared-memory atomics of the histogram (one per byte: the
+// SM retires about one warp-wide shared atomic per two cycles) and the
+// integer work of the lagged products.  Each CTA keeps a private histogram
+// in shared memory laid out as [bin][column], one column per lane and warp
+// parity, so the 32 atomics of a warp instruction always fall in 32
+// different banks.  Each thread reads 32-byte chunks (and, for the lagged
+// products, the 8 bytes after each) straight from global memory with
+// 16-byte loads, issuing the next chunk's loads before it counts the
+// current one; the lagged sums are formed four bytes at a time with the
+// unsigned 4-way byte dot product (__dp4a).  The ragged end of the buffer is
+// read with guarded loads.  The sum and the sum of squares are not
+// accumulated here: they follow exactly from the histogram (the host forms
+// them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,35 +27,64 @@ namespace lc {
 
 namespace {
 
-// Chunks per thread in a staged tile, tiles in flight per CTA, and the
-// resident CTAs per SM the direct kernel is compiled for (chosen by
-// measurement on GB300).
-#ifndef LC_STATS_CPT
-#define LC_STATS_CPT 2
-#endif
-#ifndef LC_STATS_STAGES
-#define LC_STATS_STAGES 2
-#endif
-#ifndef LC_STATS_MINB
-#define LC_STATS_MINB 5
-#endif
+constexpr uint32_t kChunk = 32;  // bytes per thread and count step
 
-constexpr int kThreads = 256;
-constexpr uint32_t kChunk = 32;                            // bytes per thread and count step
-constexpr int kCpt = LC_STATS_CPT;
-constexpr uint32_t kTileBytes = kCpt * kChunk * kThreads;  // bytes per staged tile
-constexpr uint32_t kCopyBytes = kTileBytes + 16;           // + the 16 bytes after it (lag partners)
-constexpr uint32_t kStageStride = kCopyBytes;              // 16-byte aligned stages
-constexpr int kStages = LC_STATS_STAGES;
-constexpr size_t kSmemBytes = (size_t)kStages * kStageStride;  // dynamic: the stages
+// The CTA's histogram, 64 KiB at the start of dynamic shared memory,
+// [bin][column] with 64 columns: the counter of bin x in column c sits at
+// byte offset (x << 8) | (c << 2), and lane l of warp w counts into column
+// l + 32 (w mod 2).  The bin is byte 1 of the offset and the column byte 0,
+// so one byte permute of the data word forms each count's offset.  (A
+// 32-column layout with a 128-byte bin stride halves the memory but needs a
+// shift and an and-or per byte; on GB300 it was 5-6 % slower.)
+extern __shared__ __align__(128) uint8_t dyn_smem[];
 
-// The CTA's histogram, [bin][lane]: the counter of bin x in lane l's column
-// sits at byte offset (x << 7) | (l << 2), so the 32 atomics of a warp
-// instruction fall in 32 different banks.  A static array, so that its
-// address is a constant and each count needs one shift and one and-or.
-__shared__ __align__(128) uint32_t s_hist[256 * 32];
-constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier waits
-constexpr int kTimeoutWord = 256;          // acc[256]: set when a wait gave up
+struct Hist {
+  static constexpr uint32_t kCols = 64;
+  static constexpr size_t kBytes = (size_t)256 * kCols * 4;
+
+  __device__ __forceinline__ static uint32_t* words() { return reinterpret_cast<uint32_t*>(dyn_smem); }
+  // this thread's column, as a byte offset (< 256)
+  __device__ __forceinline__ static uint32_t col4() {
+    return ((((threadIdx.x >> 5) & 1u) << 5) | (threadIdx.x & 31u)) << 2;
+  }
+  __device__ __forceinline__ static void count_at(uint32_t off) {
+    atomicAdd(reinterpret_cast<uint32_t*>(dyn_smem + off), 1u);
+  }
+  // one byte x < 256
+  __device__ __forceinline__ static void count(uint32_t x, uint32_t col) { count_at((x << 8) | col); }
+  // the 32 bytes w[0..7]; col = col4()
+  __device__ __forceinline__ static void chunk(uint32_t col, const uint32_t (&w)[10]) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      // offset byte 0 = the column (byte 0 of col), byte 1 = byte k of w[j],
+      // bytes 2-3 = byte 1 of col (zero)
+      count_at(__byte_perm(w[j], col, 0x5504u));
+      count_at(__byte_perm(w[j], col, 0x5514u));
+      count_at(__byte_perm(w[j], col, 0x5524u));
+      count_at(__byte_perm(w[j], col, 0x5534u));
+    }
+  }
+  __device__ __forceinline__ static void clear(int nthreads) {
+    uint32_t* const h = words();
+    for (int i = threadIdx.x; i < (int)(256 * kCols); i += nthreads) h[i] = 0u;
+  }
+  // after a barrier: add bin b's columns into acc[b], starting at a
+  // bin-dependent column so the threads of a warp hit different banks
+  __device__ __forceinline__ static void flush(unsigned long long* acc, int nthreads) {
+    const uint32_t* const h = words();
+    for (uint32_t b = threadIdx.x; b < 256; b += nthreads) {
+      uint64_t t = 0;
+      for (uint32_t c = 0; c < kCols; c++) t += h[b * kCols + ((c + b) & (kCols - 1u))];
+      if (t) atomicAdd(acc + b, (unsigned long long)t);
+    }
+  }
+};
+
+// Launch shapes, chosen by measurement on GB300 (1 GiB, ms): histogram only
+// 768 threads x 2 CTAs per SM 0.204 (1024 x 1: 0.205, 512 x 2: 0.216); with
+// 8 lags 512 x 2 0.266 (768 x 2: 0.270, 1024 x 1: 0.266-0.278).
+constexpr int kHistThreads = 768, kHistMinBlocks = 2;
+constexpr int kLagThreads = 512, kLagMinBlocks = 2;
 
 // Bytes i .. i + 3 of data as a little-endian word, 0 for bytes at or past
 // n (only for the ragged end of the buffer).
@@ -72,57 +94,6 @@ __device__ __forceinline__ uint32_t guarded_word(const uint8_t* data, uint64_t i
   for (int b = 0; b < 4; b++)
     if (i + b < n) v |= (uint32_t)data[i + b] << (8 * b);
   return v;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-// Thread 0: announce `bytes` on the barrier and start the bulk copy of
-// [src, src + bytes) into shared memory at dst.  16-byte aligned source and
-// destination, size a multiple of 16.
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-// Wait for phase `parity` of the barrier to complete; false after
-// kSpinLimit polls (each poll may itself suspend the thread for a while).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; it++) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void count_at(uint32_t off) {
-  atomicAdd(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(s_hist) + off), 1u);
-}
-
-// Histogram of the 32 bytes w[0..7] (all counted); lane4 = lane << 2.
-__device__ __forceinline__ void hist_chunk(uint32_t lane4, const uint32_t (&w)[10]) {
-#pragma unroll
-  for (int j = 0; j < 8; j++) {
-    count_at(((w[j] << 7) & 0x7F80u) | lane4);
-    count_at(((w[j] >> 1) & 0x7F80u) | lane4);
-    count_at(((w[j] >> 9) & 0x7F80u) | lane4);
-    count_at(((w[j] >> 17) & 0x7F80u) | lane4);
-  }
 }
 
 // Lagged products x_i x_{i+k}, k = 1..8, of the 32 bytes w[0..7] with their
@@ -150,173 +121,24 @@ __device__ __forceinline__ void lags_chunk(const uint32_t (&w)[10], uint32_t (&t
   }
 }
 
-// acc layout (uint64): [0, 256) histogram, 256 the timeout flag, 257 unused,
-// 258 + k - 1 for lag k = 1..max_lag: sum of x_i x_{i+k}.
+// acc layout (uint64): [0, 256) histogram, 256 and 257 unused, 258 + k - 1
+// for lag k = 1..max_lag: sum of x_i x_{i+k}.
 //
 // `data` here is 16-byte aligned; the caller's unaligned head is counted by
-// thread 0 of CTA 0 from `head` (h bytes before data).  Tiles [0, ntiles)
-// of kTileBytes are staged (each with the 16 bytes after it, all inside
-// the buffer); the rest [ntiles * kTileBytes, m) is counted by the last CTA
-// with guarded loads.
-template <bool kLags>
-__global__ void __launch_bounds__(kThreads) stats_kernel(const uint8_t* __restrict__ head, uint32_t h,
-                                                         const uint8_t* __restrict__ data, uint64_t m,
-                                                         uint64_t ntiles, uint32_t max_lag,
-                                                         unsigned long long* acc) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[kStages];
-  uint32_t* const hist = s_hist;
-  uint8_t* const stage = smem;
-  for (int i = threadIdx.x; i < 256 * 32; i += kThreads) hist[i] = 0u;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; s++) mbar_init(smem_addr(&bars[s]), 1u);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t lane4 = lane << 2;
-  uint64_t lag[LC_STATS_MAX_LAG];
-  uint32_t tl[LC_STATS_MAX_LAG];
-#pragma unroll
-  for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] = 0, tl[k] = 0;
-
-  // The unaligned head: at most 15 bytes, each with its lagged partners,
-  // which may lie in the aligned part.
-  if (h && blockIdx.x == 0 && threadIdx.x == 0) {
-    for (uint32_t i = 0; i < h; i++) {
-      const uint32_t x = head[i];
-      count_at((x << 7) | lane4);
-      if (kLags) {
-#pragma unroll
-        for (uint32_t k = 1; k <= LC_STATS_MAX_LAG; k++) {
-          const uint64_t j = (uint64_t)i + k;  // position in head + data
-          uint32_t y = 0;
-          if (j < h) y = head[j];
-          else if (j - h < m) y = data[j - h];
-          lag[k - 1] += (uint64_t)x * y;
-        }
-      }
-    }
-  }
-
-  // Staged tiles t = blockIdx.x + i * gridDim.x: a ring of kStages buffers,
-  // tile i in stage i mod kStages, its barrier completing phase
-  // (i / kStages) mod 2.
-  const uint64_t mine = ntiles > blockIdx.x ? (ntiles - blockIdx.x - 1) / gridDim.x + 1 : 0;
-  if (threadIdx.x == 0) {
-    for (uint64_t i = 0; i < (uint64_t)kStages && i < mine; i++)
-      bulk_load(smem_addr(stage + i * kStageStride), data + (blockIdx.x + i * gridDim.x) * (uint64_t)kTileBytes,
-                kCopyBytes, smem_addr(&bars[i]));
-  }
-  uint64_t done = 0;
-  bool timed_out = false;
-  for (uint64_t i = 0; i < mine; i++) {
-    const int s = (int)(i % kStages);
-    const bool ok = mbar_wait(smem_addr(&bars[s]), (uint32_t)((i / kStages) & 1u));
-    if (__syncthreads_or(!ok)) {  // the whole CTA leaves together
-      timed_out = true;
-      break;
-    }
-    const uint8_t* st = stage + s * kStageStride;
-#pragma unroll
-    for (int c = 0; c < kCpt; c++) {
-      const uint32_t off = (threadIdx.x + c * kThreads) * kChunk;
-      uint32_t w[10];
-      const uint4 a = *reinterpret_cast<const uint4*>(st + off);
-      const uint4 b = *reinterpret_cast<const uint4*>(st + off + 16);
-      const uint2 n8 = *reinterpret_cast<const uint2*>(st + off + 32);
-      w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
-      w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
-      w[8] = n8.x, w[9] = n8.y;
-      hist_chunk(lane4, w);
-      if (kLags) lags_chunk(w, tl);
-    }
-    // 32-bit partials: one tile adds kCpt x 32 products below 2^16 per lag,
-    // so 256 / kCpt tiles stay below 2^32
-    static_assert(kCpt == 1 || kCpt == 2 || kCpt == 4, "flush period");
-    if ((i & (256u / kCpt - 1u)) == 256u / kCpt - 1u) {
-#pragma unroll
-      for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k], tl[k] = 0;
-    }
-    done = i + 1;
-    __syncthreads();  // every thread is done with stage s
-    if (threadIdx.x == 0 && i + kStages < mine) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bulk_load(smem_addr(stage + s * kStageStride),
-                data + (blockIdx.x + (i + kStages) * gridDim.x) * (uint64_t)kTileBytes, kCopyBytes,
-                smem_addr(&bars[s]));
-    }
-  }
-  if (timed_out) {
-    // Record the failure and wait (bounded) for the copies still in flight
-    // before the CTA's shared memory is released.
-    if (threadIdx.x == 0) {
-      atomicOr(acc + kTimeoutWord, 1ull);
-      for (uint64_t i = done; i < mine && i < done + kStages; i++)
-        mbar_wait(smem_addr(&bars[i % kStages]), (uint32_t)((i / kStages) & 1u));
-    }
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k], tl[k] = 0;
-
-  // The rest of the buffer (< one tile + 32 bytes) on the last CTA, with
-  // guarded loads: bytes at or past m read as 0 and are not counted.
-  if (blockIdx.x == gridDim.x - 1) {
-    for (uint64_t i = ntiles * kTileBytes + (uint64_t)kChunk * threadIdx.x; i < m;
-         i += (uint64_t)kChunk * kThreads) {
-      uint32_t w[10];
-#pragma unroll
-      for (int j = 0; j < 10; j++) w[j] = guarded_word(data, i + 4 * j, m);
-      if (i + kChunk <= m) {
-        hist_chunk(lane4, w);
-      } else {
-        for (uint32_t q = 0; i + q < m; q++) count_at((((w[q >> 2] >> (8 * (q & 3))) & 255u) << 7) | lane4);
-      }
-      if (kLags) lags_chunk(w, tl);
-    }
-#pragma unroll
-    for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += tl[k];
-  }
-  __syncthreads();
-  // bin b: the 32 columns, read starting at a thread-dependent column so the
-  // threads of a warp hit different banks
-  for (uint32_t b = threadIdx.x; b < 256; b += kThreads) {
-    uint64_t t = 0;
-    for (uint32_t c = 0; c < 32; c++) t += hist[b * 32u + ((c + b) & 31u)];
-    if (t) atomicAdd(acc + b, (unsigned long long)t);
-  }
-  // warp-reduce the lagged sums, then one atomic per warp and lag
-  if (kLags) {
-    for (int off = 16; off; off >>= 1) {
-#pragma unroll
-      for (int k = 0; k < LC_STATS_MAX_LAG; k++) lag[k] += __shfl_down_sync(0xFFFFFFFFu, lag[k], off);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < LC_STATS_MAX_LAG; k++)
-        if (k < (int)max_lag) atomicAdd(acc + 258 + k, (unsigned long long)lag[k]);
-    }
-  }
-}
-
-// Direct variant: each thread reads its 32-byte chunks (and the 8 bytes
-// after each) straight from global memory with 16-byte loads, issuing the
-// next chunk's loads before it counts the current one, so that no shared
-// memory bandwidth goes to staging.  Chunks [0, nchunks) lie, with their 8
-// successors, inside the aligned part; the rest is counted by the last CTA
-// with guarded loads.  The lagged sums stay in 32-bit registers and reach
-// the 64-bit totals by global atomics: every 1024 chunks (a chunk adds less
-// than 2^21 per lag) and at the end, warp-reduced.
-template <bool kLags>
-__global__ void __launch_bounds__(kThreads, LC_STATS_MINB) stats_direct_kernel(
+// thread 0 of CTA 0 from `head` (h bytes before data).  Chunk c reads bytes
+// [32c, 32c + 40) of the aligned part: chunks [0, nchunks) lie, with their
+// 8 successors, inside it; the rest is counted by the last CTA with guarded
+// loads.  The lagged sums stay in 32-bit registers and reach the 64-bit
+// totals by global atomics: every 1024 chunks (a chunk adds less than 2^21
+// per lag) and at the end, warp-reduced.
+template <bool kLags, int kThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) stats_kernel(
     const uint8_t* __restrict__ head, uint32_t h, const uint8_t* __restrict__ data, uint64_t m,
     uint64_t nchunks, uint32_t max_lag, unsigned long long* acc) {
-  uint32_t* const hist = s_hist;
-  for (int i = threadIdx.x; i < 256 * 32; i += kThreads) hist[i] = 0u;
+  Hist::clear(kThreads);
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t lane4 = lane << 2;
+  const uint32_t col = Hist::col4();
   uint32_t tl[LC_STATS_MAX_LAG];
 #pragma unroll
   for (int k = 0; k < LC_STATS_MAX_LAG; k++) tl[k] = 0;
@@ -325,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, LC_STATS_MINB) stats_direct_kernel(
     // the unaligned head (< 16 bytes), with partners in the aligned part
     for (uint32_t i = 0; i < h; i++) {
       const uint32_t x = head[i];
-      count_at((x << 7) | lane4);
+      Hist::count(x, col);
       if (kLags) {
 #pragma unroll
         for (uint32_t k = 1; k <= LC_STATS_MAX_LAG; k++) {
@@ -358,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, LC_STATS_MINB) stats_direct_kernel(
       b = __ldg(reinterpret_cast<const uint4*>(q + 16));
       t8 = __ldg(reinterpret_cast<const uint2*>(q + 32));
     }
-    hist_chunk(lane4, w);
+    Hist::chunk(col, w);
     if (kLags) {
       lags_chunk(w, tl);
       if ((++it & 1023u) == 0u) {
@@ -377,19 +199,15 @@ __global__ void __launch_bounds__(kThreads, LC_STATS_MINB) stats_direct_kernel(
 #pragma unroll
       for (int j = 0; j < 10; j++) w[j] = guarded_word(data, i + 4 * j, m);
       if (i + kChunk <= m) {
-        hist_chunk(lane4, w);
+        Hist::chunk(col, w);
       } else {
-        for (uint32_t q = 0; i + q < m; q++) count_at((((w[q >> 2] >> (8 * (q & 3))) & 255u) << 7) | lane4);
+        for (uint32_t q = 0; i + q < m; q++) Hist::count((w[q >> 2] >> (8 * (q & 3))) & 255u, col);
       }
       if (kLags) lags_chunk(w, tl);
     }
   }
   __syncthreads();
-  for (uint32_t bn = threadIdx.x; bn < 256; bn += kThreads) {
-    uint64_t t = 0;
-    for (uint32_t cl = 0; cl < 32; cl++) t += hist[bn * 32u + ((cl + bn) & 31u)];
-    if (t) atomicAdd(acc + bn, (unsigned long long)t);
-  }
+  Hist::flush(acc, kThreads);
   if (kLags) {
 #pragma unroll
     for (int k = 0; k < LC_STATS_MAX_LAG; k++) {
@@ -402,7 +220,6 @@ __global__ void __launch_bounds__(kThreads, LC_STATS_MINB) stats_direct_kernel(
 
 }  // namespace
 
-// acc[256] != 0 after the kernel: a bounded wait gave up (LC_ERR_TIMEOUT).
 cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsigned long long* acc,
                          int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(acc, 0, (258 + LC_STATS_MAX_LAG) * sizeof(unsigned long long), s);
@@ -411,37 +228,26 @@ cudaError_t launch_stats(const uint8_t* data, uint64_t n, uint32_t max_lag, unsi
   const uint32_t h = (uint32_t)(mis ? (16u - mis < n ? 16u - mis : n) : 0u);
   const uint8_t* body = data + h;
   const uint64_t m = n - h;
-  // staged tiles: tile t and the 16 bytes after it lie inside the first
-  // m16 = m rounded down to 16 bytes
-  const uint64_t m16 = m & ~(uint64_t)15;
-  if (max_lag == 0) {
-    // histogram only: the direct kernel; chunk c reads bytes [32c, 32c + 40)
-    // of the aligned part
-    const uint64_t nchunks = m >= 40 ? (m - 8) / kChunk : 0;
-    const void* fnd = reinterpret_cast<const void*>(&stats_direct_kernel<false>);
-    int per_sm_d = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_d, fnd, kThreads, 0);
-    if (e != cudaSuccess) return e;
-    uint64_t grid_d = (uint64_t)sms * (uint64_t)(per_sm_d > 0 ? per_sm_d : 1);
-    const uint64_t need = (nchunks + kThreads - 1) / kThreads;
-    if (need < grid_d) grid_d = need;
-    if (grid_d == 0) grid_d = 1;
-    stats_direct_kernel<false><<<(unsigned)grid_d, kThreads, 0, s>>>(data, h, body, m, nchunks, 0, acc);
-    return cudaGetLastError();
-  }
-  // with lagged products: the staged kernel
-  const uint64_t ntiles = m16 >= 16 ? (m16 - 16) / kTileBytes : 0;
-  const void* fn = reinterpret_cast<const void*>(&stats_kernel<true>);
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  const uint64_t nchunks = m >= 40 ? (m - 8) / kChunk : 0;
+  const void* fn = max_lag ? reinterpret_cast<const void*>(&stats_kernel<true, kLagThreads, kLagMinBlocks>)
+                           : reinterpret_cast<const void*>(&stats_kernel<false, kHistThreads, kHistMinBlocks>);
+  const int threads = max_lag ? kLagThreads : kHistThreads;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Hist::kBytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, kSmemBytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, Hist::kBytes);
   if (e != cudaSuccess) return e;
-  // one wave of resident CTAs, at most one per tile
+  // one wave of resident CTAs, no more than the chunks need
   uint64_t grid = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
-  if (ntiles < grid) grid = ntiles;
+  const uint64_t need = (nchunks + threads - 1) / threads;
+  if (need < grid) grid = need;
   if (grid == 0) grid = 1;
-  stats_kernel<true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(data, h, body, m, ntiles, max_lag, acc);
+  if (max_lag)
+    stats_kernel<true, kLagThreads, kLagMinBlocks>
+        <<<(unsigned)grid, kLagThreads, Hist::kBytes, s>>>(data, h, body, m, nchunks, max_lag, acc);
+  else
+    stats_kernel<false, kHistThreads, kHistMinBlocks>
+        <<<(unsigned)grid, kHistThreads, Hist::kBytes, s>>>(data, h, body, m, nchunks, 0, acc);
   return cudaGetLastError();
 }
 
