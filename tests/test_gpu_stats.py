@@ -41,6 +41,41 @@ def test_stats_exact(ctx, n):
             assert list(st.lag_sum)[:max_lag] == lag
 
 
+def _periodic_stats(n, period, max_lag):
+    """Exact statistics of x_i = i mod period, i = 0..n-1, in closed form:
+    whole periods times the sums over one period, plus the partial one."""
+    q, r = divmod(n, period)
+    hist = [q + (1 if v < r else 0) if v < period else 0 for v in range(256)]
+    lag = []
+    for k in range(1, max_lag + 1):
+        m = max(n - k, 0)
+        qk, rk = divmod(m, period)
+        one = sum(j * ((j + k) % period) for j in range(period))
+        lag.append(qk * one + sum(j * ((j + k) % period) for j in range(rk)))
+    return hist, lag
+
+
+@pytest.mark.parametrize("shift", [0, 3])
+def test_stats_closed_form_6gib(ctx, shift):
+    # 6 GiB: every thread of both builds walks hundreds of grid strides, and
+    # the lagged build's 32-bit partials go through their periodic flush into
+    # the 64-bit totals (every 1024 chunks per thread)
+    n, period = 6 << 30, 251
+    buf = torch.empty(n + 16, dtype=torch.uint8, device="cuda")
+    pat = torch.arange(period, device="cuda").to(torch.uint8)
+    reps = (n + period - 1) // period
+    buf[shift:shift + n] = pat.repeat(reps)[:n]
+    for max_lag in (0, 8):
+        st = lc.lc_byte_stats(ctx.handle, buf.data_ptr() + shift, n, max_lag)
+        hist, lag = _periodic_stats(n, period, max_lag)
+        assert st.n == n
+        assert list(st.hist) == hist
+        assert st.sum == sum(v * c for v, c in enumerate(hist))
+        assert list(st.lag_sum)[:max_lag] == lag
+    del buf
+    torch.cuda.empty_cache()
+
+
 def test_ciphertext_statistics(ctx):
     # Sec. 4: the ciphertext histogram is flat and carries no correlation
     # between neighbouring bytes; two close passwords give unrelated
