@@ -426,7 +426,11 @@ enum {
   LC_SFP_MUL28 = 4,   /* 28 * a */
   LC_SFP_FLOOR13 = 5, /* low 32 bits of floor(RN(a * 10^13)) */
   LC_SFP_MULDT = 6,   /* 0.01 * a (the compile-time constant multiply) */
-  LC_SFP_MULBETA = 7  /* RN(8/3) * a (the same) */
+  LC_SFP_MULBETA = 7, /* RN(8/3) * a (the same) */
+  LC_SFP_ADD_KICK = 8, /* a + b by the known-order adder for a larger than
+                          b >= 0 (the kick of Step 2) */
+  LC_SFP_ADD_Z = 9     /* a + b by the known-order adder for a > 0 larger than
+                          b (the Euler step's z update) */
 };
 lc_status lc_softfp_eval(uint32_t op, const uint64_t* a_dev, const uint64_t* b_dev, uint64_t* sw_dev,
                          uint64_t* hw_dev, size_t n, void* stream);

@@ -23,15 +23,16 @@
 
 // Binary64 operations of the v1 fast path computed on the integer pipe
 // (bit mask, see kEmu* below): the eight Euler multiplies, the alpha
-// scaling and the kick.  Chosen by measurement on GB300.
+// scaling and the kick (by the known-order adder).  Chosen by measurement
+// on GB300.
 #ifndef LC_EMU_MASK
-#define LC_EMU_MASK 0x80FFu
+#define LC_EMU_MASK 0x280FFu
 #endif
 // The same for the warm-up steps before the first byte (they carry no
 // per-byte bookkeeping, so their best split can differ): the eight
-// multiplies and the z update.
+// multiplies and the z update (by the known-order adder).
 #ifndef LC_WARM_MASK
-#define LC_WARM_MASK 0x40FFu
+#define LC_WARM_MASK 0x440FFu
 #endif
 // The byte steps of batches that leave the persistent grid partly empty:
 // the eight multiplies and the alpha scaling (the emulated kick lengthens
@@ -39,9 +40,10 @@
 #ifndef LC_PARTIAL_MASK
 #define LC_PARTIAL_MASK 0xFFu
 #endif
-// and their warm-up steps
+// and their warm-up steps: the multiplies and the z update, as in the
+// full-grid warm-up
 #ifndef LC_PARTIAL_WARM_MASK
-#define LC_PARTIAL_WARM_MASK 0xFFu
+#define LC_PARTIAL_WARM_MASK 0x440FFu
 #endif
 // Minimum resident 256-thread CTAs per SM the v1 kernel is compiled for
 // (bounds its registers per thread).  Chosen by measurement on GB300.
@@ -76,6 +78,11 @@ enum : uint32_t {
   kEmuAddZ = 1u << 14,
   kEmuKick = 1u << 15,
   kEmuAprime = 1u << 16,
+  // with kEmuKick / kEmuAddZ: that addition by the known-order adder
+  // (sfp::dadd_small) instead of the general one; the kick adds Theta >= 0
+  // to a coordinate larger than it, the z update dt dz (either sign) to z > 0
+  kEmuOrderedKick = 1u << 17,
+  kEmuOrderedAddZ = 1u << 18,
 };
 
 template <bool SW>
@@ -138,7 +145,9 @@ __device__ __forceinline__ void euler_v1(double& x, double& y, double& z, double
   const double dz = f_sub<(M & kEmuSubBZ) != 0>(xy, bz);
   x = f_add<(M & kEmuAddX) != 0>(x, mul_dt<(M & kEmuMulDtX) != 0>(dt, dx));
   y = f_add<(M & kEmuAddY) != 0>(y, mul_dt<(M & kEmuMulDtY) != 0>(dt, dy));
-  z = f_add<(M & kEmuAddZ) != 0>(z, mul_dt<(M & kEmuMulDtZ) != 0>(dt, dz));
+  const double dtdz = mul_dt<(M & kEmuMulDtZ) != 0>(dt, dz);
+  z = (M & kEmuAddZ) && (M & kEmuOrderedAddZ) ? sfp::dadd_small<true, false>(z, dtdz)
+                                              : f_add<(M & kEmuAddZ) != 0>(z, dtdz);
 }
 
 // floor(RN(alpha * 10^13)) as a two's complement int64: cvt.rmi.s64.f64
@@ -381,7 +390,9 @@ struct V1Path {
     const uint32_t s = R1 + R2;
     const uint32_t out = (dec ? (in - s) : (in + s)) & 255u;
     const uint32_t P = dec ? out : in;
-    const double kicked = f_add<(M & kEmuKick) != 0>(pick(mu2, x, y, z), theta[om2 * 256u + P]);
+    const double th = theta[om2 * 256u + P];
+    const double kicked = (M & kEmuKick) && (M & kEmuOrderedKick) ? sfp::dadd_small<false, true>(pick(mu2, x, y, z), th)
+                                                                  : f_add<(M & kEmuKick) != 0>(pick(mu2, x, y, z), th);
     x = mu2 == 0 ? kicked : x;
     y = mu2 == 1 ? kicked : y;
     z = mu2 == 2 ? kicked : z;

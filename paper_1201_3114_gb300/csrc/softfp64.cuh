@@ -169,6 +169,34 @@ __device__ __forceinline__ double dmul_const(double a) {
   return dmul_fields(xl, xh, yl, b1, er, xh & 0x80000000u);
 }
 
+// The adders' shared core.  add_aligned: X1:X0 + Y or X1:X0 - Y (sub = 1),
+// where Y is Y1:Y0 shifted right by the gap d < 32 with every bit shifted
+// out folded into its bit 0 (sticky).  add_round_pack: R is that sum, its
+// leading bit at 63 - lz (lz <= 2); keep the 53 bits from the leading one,
+// round half to even, and pack with the sign bit and the biased exponent ex
+// of the larger operand.
+__device__ __forceinline__ uint64_t add_aligned(uint32_t X1, uint32_t X0, uint32_t Y1, uint32_t Y0, uint32_t d,
+                                                uint32_t sub) {
+  const uint32_t s0 = __funnelshift_r(Y0, Y1, d), s1 = Y1 >> d;
+  const uint32_t lost = Y0 & ((1u << d) - 1u);
+  // X + Y, or X - Y as X + ~Y + 1
+  const uint32_t m = 0u - sub;
+  const uint32_t t0 = (s0 | (lost != 0u ? 1u : 0u)) ^ m, t1 = s1 ^ m;
+  return ((((uint64_t)X1 << 32) | X0) + (((uint64_t)t1 << 32) | t0)) + sub;
+}
+__device__ __forceinline__ double add_round_pack(uint64_t R, uint32_t ex, uint32_t sign) {
+  // leading bit at 63 - lz; the result's biased exponent is ex + 1 - lz
+  const uint32_t lz = __clz((uint32_t)(R >> 32));
+  const uint32_t rp = 11u - lz;  // bits below the last kept place
+  const uint32_t last = ((uint32_t)R >> rp) & 1u;
+  const uint64_t T = R + ((1u << (rp - 1u)) - 1u + last);
+  const uint32_t T1 = (uint32_t)(T >> 32), T0 = (uint32_t)T;
+  const uint32_t q0 = __funnelshift_r(T0, T1, rp), q1 = T1 >> rp;
+  // q has its hidden bit at 2^52 (2^53 after a rounding carry), which
+  // supplies the last 1 of the exponent field (or steps to the next binade)
+  return pack(sign + ((ex - lz) << 20) + q1, q0);
+}
+
 // RN(a + b) for two normal operands (either sign) with a normal result.
 // Subtraction of operands whose exponents differ by at most one can cancel
 // many leading bits; that case, and exponent gaps of 32 or more (where b
@@ -198,26 +226,40 @@ __device__ __forceinline__ double dadd(double a, double b) {
   const uint32_t xm = (xh & 0xFFFFFu) | 0x100000u, ym = (yh & 0xFFFFFu) | 0x100000u;
   const uint32_t X1 = __funnelshift_l(xl, xm, 10), X0 = xl << 10;
   const uint32_t Y1 = __funnelshift_l(yl, ym, 10), Y0 = yl << 10;
-  const uint32_t s0 = __funnelshift_r(Y0, Y1, d), s1 = Y1 >> d;
-  const uint32_t lost = Y0 & ((1u << d) - 1u);
-  // X + Y, or X - Y as X + ~Y + 1
-  const uint32_t m = 0u - sub;
-  const uint32_t t0 = (s0 | (lost != 0u ? 1u : 0u)) ^ m, t1 = s1 ^ m;
-  const uint64_t R = ((((uint64_t)X1 << 32) | X0) + (((uint64_t)t1 << 32) | t0)) + sub;
-  // leading bit at 63 - lz; the result's biased exponent is ex + 1 - lz
-  const uint32_t lz = __clz((uint32_t)(R >> 32));
-  const uint32_t rp = 11u - lz;  // bits below the last kept place
-  const uint32_t last = ((uint32_t)R >> rp) & 1u;
-  const uint64_t T = R + ((1u << (rp - 1u)) - 1u + last);
-  const uint32_t T1 = (uint32_t)(T >> 32), T0 = (uint32_t)T;
-  const uint32_t q0 = __funnelshift_r(T0, T1, rp), q1 = T1 >> rp;
-  // q has its hidden bit at 2^52 (2^53 after a rounding carry), which
-  // supplies the last 1 of the exponent field (or steps to the next binade)
-  const uint32_t hi = (xh & 0x80000000u) + ((ex - lz) << 20) + q1;
-  return pack(hi, q0);
+  return add_round_pack(add_aligned(X1, X0, Y1, Y0, d, sub), ex, xh & 0x80000000u);
 }
 
 __device__ __forceinline__ double dsub(double a, double b) { return dadd(a, -b); }
+
+// RN(x + a) where x is the larger operand in magnitude, by an exponent gap
+// d of 1..31 (2..31 when the signs differ, so at most one leading bit
+// cancels): dadd with the operand order known, so no comparison or swap.
+// kXPos / kAPos: the caller expects x / a to be positive; the fast path then
+// checks that sign and leaves it out of the sign logic.  Every other case
+// (an operand zero, subnormal or not finite, x in the top binade, a gap
+// outside the range, an operand of the other sign) goes to the hardware,
+// except x + 0 = x for a normal x.
+template <bool kXPos, bool kAPos>
+__device__ __forceinline__ double dadd_small(double x, double a) {
+  const uint32_t xh = hi32(x), xl = lo32(x), ah = hi32(a), al = lo32(a);
+  // with the sign bit kept, a negative operand gives an exponent >= 2048,
+  // which fails the range checks below
+  const uint32_t ex = kXPos ? xh >> 20 : (xh >> 20) & 0x7FFu;
+  const uint32_t ea = kAPos ? ah >> 20 : (ah >> 20) & 0x7FFu;
+  const uint32_t sub = (kXPos ? 0u : xh >> 31) ^ (kAPos ? 0u : ah >> 31);
+  const uint32_t d = ex - ea;
+  // d in [1 + sub, 31]; unsigned wrap-around sends d <= sub to the hardware
+  const bool fast = ea != 0u && ex <= 2045u && d - 1u - sub <= 30u - sub;
+  if (!fast) {
+    // x + 0 = x for a normal x (the cipher's kick adds +0 for a zero byte)
+    if (((ah & 0x7FFFFFFFu) | al) == 0u && ((xh >> 20) & 0x7FFu) - 1u <= 2045u) return x;
+    return hw_add(x, a);
+  }
+  const uint32_t xm = (xh & 0xFFFFFu) | 0x100000u, am = (ah & 0xFFFFFu) | 0x100000u;
+  const uint32_t X1 = __funnelshift_l(xl, xm, 10), X0 = xl << 10;
+  const uint32_t Y1 = __funnelshift_l(al, am, 10), Y0 = al << 10;
+  return add_round_pack(add_aligned(X1, X0, Y1, Y0, d, sub), ex, xh & 0x80000000u);
+}
 
 }  // namespace sfp
 }  // namespace lc

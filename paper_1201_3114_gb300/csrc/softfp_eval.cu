@@ -34,6 +34,8 @@ __global__ void eval_kernel(uint32_t op, const uint64_t* __restrict__ a, const u
         s = S::bits(S::dmul_const<0x4005555555555555ull>(x));
         h = S::bits(__dmul_rn(x, 8.0 / 3.0));
         break;
+      case LC_SFP_ADD_KICK: s = S::bits(S::dadd_small<false, true>(x, y)); h = S::bits(__dadd_rn(x, y)); break;
+      case LC_SFP_ADD_Z: s = S::bits(S::dadd_small<true, false>(x, y)); h = S::bits(__dadd_rn(x, y)); break;
       default: break;
     }
     sw[i] = s;
@@ -45,9 +47,9 @@ __global__ void eval_kernel(uint32_t op, const uint64_t* __restrict__ a, const u
 
 extern "C" lc_status lc_softfp_eval(uint32_t op, const uint64_t* a_dev, const uint64_t* b_dev,
                                     uint64_t* sw_dev, uint64_t* hw_dev, size_t n, void* stream) {
-  if (op > LC_SFP_MULBETA) return LC_ERR_ARG;
+  if (op > LC_SFP_ADD_Z) return LC_ERR_ARG;
   if (n && (!a_dev || !sw_dev || !hw_dev)) return LC_ERR_ARG;
-  if (n && !b_dev && op <= LC_SFP_MUL) return LC_ERR_ARG;
+  if (n && !b_dev && (op <= LC_SFP_MUL || op >= LC_SFP_ADD_KICK)) return LC_ERR_ARG;
   if (n == 0) return LC_OK;
   eval_kernel<<<1024, 256, 0, static_cast<cudaStream_t>(stream)>>>(op, a_dev, b_dev, sw_dev, hw_dev, n);
   return cudaGetLastError() == cudaSuccess ? LC_OK : LC_ERR_CUDA;

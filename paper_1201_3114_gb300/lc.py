@@ -553,7 +553,8 @@ def lc_probe_pipes(device: int = 0) -> lc_pipe_rates:
     return r
 
 
-LC_SFP_ADD, LC_SFP_SUB, LC_SFP_MUL, LC_SFP_MUL10, LC_SFP_MUL28, LC_SFP_FLOOR13, LC_SFP_MULDT, LC_SFP_MULBETA = range(8)
+(LC_SFP_ADD, LC_SFP_SUB, LC_SFP_MUL, LC_SFP_MUL10, LC_SFP_MUL28, LC_SFP_FLOOR13, LC_SFP_MULDT, LC_SFP_MULBETA,
+ LC_SFP_ADD_KICK, LC_SFP_ADD_Z) = range(10)
 
 
 def lc_softfp_eval(op, a_dev, b_dev, sw_dev, hw_dev, n, stream=None) -> int:

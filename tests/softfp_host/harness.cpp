@@ -2,8 +2,10 @@
 // csrc/softfp64.cuh, compiled for the host, against the host's IEEE-754
 // arithmetic: round to nearest, ties to even (IEEE 754-2019 Sec. 4.3.1) for
 // a + b, a - b, a * b, 10 a, 28 a, 0.01 a and RN(8/3) a (the multiplies by
-// a compile-time constant), and floor(RN(a * 10^13)) converted to int64 with
-// saturation (low 32 bits) for the scaled floor.
+// a compile-time constant), a + b by the two known-order adders (the
+// kick's, for a larger than b >= 0, and the z update's, for a > 0 larger
+// than b), and floor(RN(a * 10^13)) converted to int64 with saturation (low
+// 32 bits) for the scaled floor.
 //
 // Operands come from generated classes (a full grid of exponent pairs,
 // the cipher's value range, every adder gap with tie and sticky bit
@@ -34,8 +36,9 @@ namespace S = lc::sfp;
 
 namespace {
 
-enum Op { ADD, SUB, MUL, MUL10, MUL28, FLOOR13, MULDT, MULBETA, NOPS };
-const char* const kOpName[NOPS] = {"add", "sub", "mul", "mul10", "mul28", "floor13", "muldt", "mulbeta"};
+enum Op { ADD, SUB, MUL, MUL10, MUL28, FLOOR13, MULDT, MULBETA, ADDKICK, ADDZ, NOPS };
+const char* const kOpName[NOPS] = {"add",    "sub",     "mul",     "mul10",   "mul28",
+                                   "floor13", "muldt", "mulbeta", "addkick", "addz"};
 
 // the constants of the constant-operand multiplies and their bit patterns
 constexpr double kDt = 0.01;
@@ -127,6 +130,8 @@ uint64_t ref(Op op, double a, double b) {
     case FLOOR13: return ref_floor13(a);
     case MULDT: return to_bits(a * kDt);
     case MULBETA: return to_bits(a * kBeta);
+    case ADDKICK:
+    case ADDZ: return to_bits(a + b);
     default: return 0;
   }
 }
@@ -141,6 +146,8 @@ uint64_t soft(Op op, double a, double b) {
     case FLOOR13: return S::floor_scaled_lo32(a);
     case MULDT: return S::bits(S::dmul_const<kDtBits>(a));
     case MULBETA: return S::bits(S::dmul_const<kBetaBits>(a));
+    case ADDKICK: return S::bits(S::dadd_small<false, true>(a, b));
+    case ADDZ: return S::bits(S::dadd_small<true, false>(a, b));
     default: return 0;
   }
 }
@@ -154,8 +161,10 @@ bool is_tie(Op op, double a, double b) {
   double r, e;
   switch (op) {
     case ADD:
-    case SUB: {
-      const double y = op == ADD ? b : -b;
+    case SUB:
+    case ADDKICK:
+    case ADDZ: {
+      const double y = op == SUB ? -b : b;
       r = a + y;
       const double bb = r - a;
       e = (a - (r - bb)) + (y - bb);
@@ -229,6 +238,11 @@ std::vector<ClassDef> classes(Op op) {
     return {{"exp_grid", 2048ull * 2048 * 2}, {"cipher", 2u << 20}, {"wide", 1u << 20},
             {"few_bits", 1u << 20},          {"gap", 4u << 20},    {"cancel", 2u << 20},
             {"ties", 2u << 20},              {"ties_far", 1u << 20}};
+  if (op == ADDKICK || op == ADDZ)
+    return {{"exp_grid", 2048ull * 2048}, {"cipher", 1u << 20},   {"wide", 1u << 20},
+            {"few_bits", 1u << 20},      {"gap", 4u << 20},      {"cancel", 2u << 20},
+            {"ties", 2u << 20},          {"ties_far", 1u << 20}, {"cipher_kick", 2u << 20},
+            {"cipher_z", 2u << 20},      {"gap1", 1u << 20},     {"zeros", 1u << 18}};
   if (op == MUL)
     return {{"exp_grid", 2048ull * 2048 * 2}, {"cipher", 2u << 20},      {"wide", 1u << 20},
             {"few_bits", 2u << 20},          {"result_edge", 2u << 20}, {"cipher_consts", 2u << 20}};
@@ -241,7 +255,59 @@ std::vector<ClassDef> classes(Op op) {
   return {{"exp_grid", 2048ull * 2 * 512}, {"cipher", 4u << 20}, {"wide", 1u << 20}, {"few_bits", 1u << 20}};
 }
 
+void gen_class(Op op, const char* cls, uint64_t i, Gen& g, double* a, double* b);
+
+// Operands of the known-order adders: the classes of the general adder, put
+// in the order and signs the routine expects (a larger, and b >= 0 for the
+// kick's, a > 0 for the z update's) in 9 of 10 cases, the rest left as drawn
+// (they must take the hardware path); and the cipher's own operands.
 void gen(Op op, const char* cls, uint64_t i, Gen& g, double* a, double* b) {
+  if (op == ADDKICK && !strcmp(cls, "cipher_kick")) {
+    static const double kTen[4] = {1e3, 1e4, 1e5, 1e6};
+    *a = g.unit() * 120.0 - 60.0;
+    *b = (double)g.below(256) / kTen[g.below(4)];
+    return;
+  }
+  if (op == ADDZ && !strcmp(cls, "cipher_z")) {
+    *a = 2.0 + g.unit() * 46.0;
+    *b = g.unit() * 6.0 - 3.0;
+    return;
+  }
+  if ((op == ADDKICK || op == ADDZ) && !strcmp(cls, "gap1")) {
+    // a just above a power of two, b of the other sign just below it: gap
+    // one, many leading bits cancel (the hardware's case)
+    const int e = g.range(-1000, 1000);
+    const double m = 1.0 + g.unit() * ldexp(1.0, -g.range(1, 52));
+    const double n = 2.0 - (0.5 + 0.5 * g.unit()) * ldexp(1.0, -g.range(0, 52));
+    *a = ldexp(m, e);
+    *b = -ldexp(n, e - 1);
+    if (op == ADDKICK) {
+      *a = -*a;
+      *b = -*b;
+    }
+    return;
+  }
+  if ((op == ADDKICK || op == ADDZ) && !strcmp(cls, "zeros")) {
+    // a zero addend: x + 0 = x only for x nonzero; -0 + 0 = +0
+    static const double kX[8] = {0.0, -0.0, 5e-324, -5e-324, 1.0, -2.5, INFINITY, NAN};
+    *a = g.below(2) ? kX[g.below(8)] : cipher_value(g);
+    *b = g.below(2) ? 0.0 : -0.0;
+    return;
+  }
+  if ((op == ADDKICK && !strcmp(cls, "cipher_z")) || (op == ADDZ && !strcmp(cls, "cipher_kick"))) {
+    // the other routine's operands
+    gen(op == ADDKICK ? ADDZ : ADDKICK, cls, i, g, a, b);
+    return;
+  }
+  gen_class(op == ADDKICK || op == ADDZ ? ADD : op, cls, i, g, a, b);
+  if ((op == ADDKICK || op == ADDZ) && g.below(10) != 0) {
+    if (fabs(*a) < fabs(*b)) std::swap(*a, *b);
+    if (op == ADDKICK) *b = fabs(*b);
+    else *a = fabs(*a);
+  }
+}
+
+void gen_class(Op op, const char* cls, uint64_t i, Gen& g, double* a, double* b) {
   const bool two = op == ADD || op == SUB || op == MUL;
   *b = 0.0;
   if ((op == MULDT || op == MULBETA) && !strcmp(cls, "ties")) {

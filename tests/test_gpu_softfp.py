@@ -75,7 +75,7 @@ def rng():
     return np.random.default_rng(1234)
 
 
-@pytest.mark.parametrize("op", [lc.LC_SFP_ADD, lc.LC_SFP_SUB, lc.LC_SFP_MUL])
+@pytest.mark.parametrize("op", [lc.LC_SFP_ADD, lc.LC_SFP_SUB, lc.LC_SFP_MUL, lc.LC_SFP_ADD_KICK, lc.LC_SFP_ADD_Z])
 def test_two_operand_routines_random(rng, op):
     a = _operands(rng, N)
     b = _operands(rng, N)
@@ -107,6 +107,44 @@ def test_adder_every_exponent_gap_and_cancellation(rng):
     t = np.ldexp(rng.integers(2 ** 52, 2 ** 53, n).astype(np.float64), k - 52)
     h = np.ldexp(1.0, k - 53) * rng.choice([1.0, 3.0, -1.0, -3.0], n)
     _check(lc.LC_SFP_ADD, _f64(t), _f64(h))
+
+
+def test_known_order_adders(rng):
+    """The kick's adder (a larger than b >= 0) and the z update's (a > 0
+    larger than b): the cipher's own operands, every gap with both signs,
+    near-cancellation, exact ties, and operands in the wrong order or with
+    the wrong sign (which must take the hardware path)."""
+    n = 1 << 20
+    # the kick: a coordinate and Theta = P / 10^(3 + Omega)
+    x = rng.uniform(-60, 60, n)
+    P = rng.integers(0, 256, n).astype(np.float64)
+    theta = P / np.array([1e3, 1e4, 1e5, 1e6])[rng.integers(0, 4, n)]
+    _check(lc.LC_SFP_ADD_KICK, _f64(x), _f64(theta))
+    # the z update: z and dt dz of either sign
+    z = rng.uniform(0.5, 50, n)
+    dz = rng.uniform(-6, 6, n)
+    _check(lc.LC_SFP_ADD_Z, _f64(z), _f64(dz))
+    a = np.ldexp(rng.uniform(1, 2, n), rng.integers(-30, 30, n))
+    gap = rng.integers(-3, 40, n)
+    b = np.ldexp(rng.uniform(1, 2, n), np.frexp(a)[1] - 1 - gap)
+    sa, sb = rng.choice([-1.0, 1.0], n), rng.choice([-1.0, 1.0], n)
+    for op in (lc.LC_SFP_ADD_KICK, lc.LC_SFP_ADD_Z):
+        _check(op, _f64(a), _f64(b))
+        _check(op, _f64(a * sa), _f64(b))
+        _check(op, _f64(a), _f64(b * sb))
+        _check(op, _f64(a * sa), _f64(b * sb))
+        # near-cancellation and exact halfway sums
+        ai = _f64(a)
+        pert = ai ^ rng.integers(0, 1 << 12, n, dtype=np.uint64)
+        _check(op, ai, pert ^ np.uint64(1 << 63))
+        k = rng.integers(-40, 40, n)
+        t = np.ldexp(rng.integers(2 ** 52, 2 ** 53, n).astype(np.float64), k - 52)
+        h = np.ldexp(1.0, k - 53) * rng.choice([1.0, 3.0, -1.0, -3.0], n)
+        _check(op, _f64(t), _f64(h))
+        _check(op, _f64(t), _f64(np.abs(h)))
+        # zero addends: x + 0 = x, and -0 + 0 = +0
+        _check(op, _f64(np.r_[x, -0.0, 0.0, 5e-324]), _f64(np.zeros(n + 3)))
+        _check(op, _f64(np.r_[x, -0.0, 0.0, 5e-324]), _f64(np.full(n + 3, -0.0)))
 
 
 def _const_ties(rng, n, c):

@@ -58,7 +58,7 @@ def test_routines_match_ieee_round_to_nearest_even(harness):
     rc, rows = _run(harness, SCALE)
     bad = {k: v for k, v in rows.items() if v["bad"]}
     assert rc == 0 and not bad, bad
-    ops = {"add", "sub", "mul", "mul10", "mul28", "floor13", "muldt", "mulbeta"}
+    ops = {"add", "sub", "mul", "mul10", "mul28", "floor13", "muldt", "mulbeta", "addkick", "addz"}
     assert {k[0] for k in rows} == ops
     for op in ops:
         cases = sum(v["cases"] for k, v in rows.items() if k[0] == op)
@@ -83,6 +83,14 @@ def test_routines_match_ieee_round_to_nearest_even(harness):
         r = rows[(op, "ties")]
         assert r["fast"] == r["cases"] == r["ties"], r
     assert rows[("add", "cipher")]["fast"] > 0.9 * rows[("add", "cipher")]["cases"]
+    # the known-order adders: the cipher's kick and z-update operands stay on
+    # the integer path, and so do the ordered tie and gap cases
+    assert rows[("addkick", "cipher_kick")]["fast"] > 0.99 * rows[("addkick", "cipher_kick")]["cases"]
+    assert rows[("addz", "cipher_z")]["fast"] > 0.9 * rows[("addz", "cipher_z")]["cases"]
+    for op in ("addkick", "addz"):
+        r = rows[(op, "ties")]
+        assert r["fast"] > 0.8 * r["cases"] and r["ties"] > 0.2 * r["cases"], (op, r)
+        assert rows[(op, "gap")]["fast"] > 0.3 * rows[(op, "gap")]["cases"], op
 
 
 MUTATIONS = [
@@ -96,6 +104,13 @@ MUTATIONS = [
     ("dadd rounds half down", "const uint64_t T = R + ((1u << (rp - 1u)) - 1u + last);",
      "const uint64_t T = R + ((1u << (rp - 1u)) - 1u);", ("add", "ties")),
     ("dadd drops the sticky bit", "(s0 | (lost != 0u ? 1u : 0u)) ^ m", "s0 ^ m", ("sub", "gap")),
+    ("the adders' shared core drops the sticky bit", "(s0 | (lost != 0u ? 1u : 0u)) ^ m", "s0 ^ m",
+     ("addkick", "gap")),
+    ("the known-order adder subtracts at a gap of one", "d - 1u - sub <= 30u - sub", "d - 1u <= 30u",
+     ("addz", "gap1")),
+    ("the known-order adder returns x + 0 = x for a zero or subnormal x",
+     "&& ((xh >> 20) & 0x7FFu) - 1u <= 2045u) return x;", ") return x;", ("addkick", "zeros")),
+    ("the known-order adder ignores the addend's sign", "(kAPos ? 0u : ah >> 31)", "0u", ("addz", "cipher_z")),
     ("floor truncates negatives", "return 0u - ip - (frac != 0u ? 1u : 0u);", "return 0u - ip;",
      ("floor13", "cipher")),
     ("mul_small rounds half up", "const uint32_t up = (rem > half || (rem == half && (q0 & 1u))) ? 1u : 0u;\n"
