@@ -761,6 +761,34 @@ def next_rows(args):
         out["s3000_profile"] = {"bytes": n, "block_len": 64, "ms": ms, "MBps": n / ms / 1e3,
                                 "euler_steps_per_s": steps / (ms * 1e-3)}
 
+    # per-request keys (row f2): 128 messages of 4 MiB (131,072 parts) whose
+    # requests carry their own k, against the same batch with the context's
+    # k = (4, 4, 4), and against the general path (small-batch threshold
+    # raised above the batch)
+    with lc.Context(0) as c:
+        nm, mb = 128, 4 << 20
+        P = torch.empty(nm * mb, dtype=torch.uint8, device="cuda")
+        lc.check(lc.lc_synth_uniform(P, P.numel(), synth.config_seed(4) + 23, 0, stream))
+        clen = c.ciphertext_len(mb)
+        Cb = torch.empty(nm * clen, dtype=torch.uint8, device="cuda")
+        st = torch.empty(nm, dtype=torch.int32, device="cuda")
+        ks = [(3, 4, 3), (3, 3, 3), (4, 3, 4), (4, 4, 4)]
+
+        def items(own_k):
+            return [(synth.password(synth.subseed(93, m), 8 + m % 25), 0, P.data_ptr() + m * mb, mb,
+                     Cb.data_ptr() + m * clen, clen, None, ks[m % 4] if own_k else None) for m in range(nm)]
+
+        rows = {}
+        for label, own_k, small in (("context_k", False, 0), ("own_k", True, 0),
+                                    ("own_k_general_path", True, 0xFFFFFFFF)):
+            lc.check(lc.lc_ctx_set_launch(c.handle, 256, 0, 0, small, 0, 1))
+            b = lc.BatchEx(items(own_k))
+            ms = timed(lambda: lc.check(lc.lc_run_batch_ex(c.handle, b, st, lc.LC_PARALLEL, stream)), 3)
+            assert int(st.max()) == 0 and int(st.min()) == 0
+            rows[label] = {"ms": ms, "GBps": nm * mb / ms / 1e6}
+        out["per_request_k_batched"] = dict(rows, messages=nm, message_bytes=mb,
+                                            keys="k in (3,4,3), (3,3,3), (4,3,4), (4,4,4) in rotation")
+
     # the delta t = 0.027 profile (the trajectory leaves the attractor and
     # saturates; every emulated operation then takes its hardware fallback)
     with lc.Context(0, lc.params(dt=0.027)) as c:

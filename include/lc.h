@@ -201,8 +201,11 @@ typedef struct {
 
 /* lc_run_batch with per-request key material: the same call, results and
  * errors, for lc_req_ex requests.  Requests of one batch may mix lambda and
- * k values; a batch in which some request's k is not (4, 4, 4) runs the
- * kernel variant that keeps all binary64 work on the FP64 pipe. */
+ * k values.  A batch in which some request's k is not (4, 4, 4) runs, with
+ * the context's v1 constants and at least the small-batch threshold of
+ * parts (lc_launch.small_batch_rows), the v1 build that reads k per message;
+ * otherwise the kernel variant that keeps all binary64 work on the FP64
+ * pipe. */
 lc_status lc_run_batch_ex(lc_ctx* ctx, const lc_req_ex* reqs, size_t count, int32_t* status_dev,
                           lc_mode m, void* stream);
 

@@ -366,18 +366,23 @@ lc_status build_graph(lc_ctx* ctx, int v) {
 // Kernel variant for a batch of nrows parts: v1 batches that cannot fill
 // the GPU run the latency variant.
 int batch_variant(const lc_ctx* ctx, size_t nrows, bool msg_k = false) {
-  // a request with its own k other than (4, 4, 4) needs the general path,
-  // which reads k per message
+  // a request with its own k other than (4, 4, 4) needs a build that reads
+  // k per message
   const bool v1 = !msg_k && ctx->variant == kVariantV1;
   if (ctx->ct_stats) {
     if (ctx->digits) return v1 ? kVariantV1DigitsCtStats : kVariantGeneralDigitsCtStats;
     return v1 ? kVariantV1CtStats : kVariantGeneralCtStats;
   }
-  if (msg_k) return ctx->digits ? kVariantGeneralDigits : kVariantGeneral;
-  if (ctx->digits) return ctx->variant == kVariantV1 ? kVariantV1Digits : kVariantGeneralDigits;
-  if (ctx->variant != kVariantV1) return ctx->variant;
   const uint64_t thr = ctx->launch.small_batch_rows ? ctx->launch.small_batch_rows
                                                     : (uint64_t)ctx->sm_count * kSmallBatchRowsPerSm;
+  if (msg_k) {
+    // k in {3, 4}^3 per message: the v1 build that reads k per message for
+    // batches that fill the GPU, the general path for the rest
+    if (ctx->digits) return kVariantGeneralDigits;
+    return ctx->variant == kVariantV1 && nrows >= thr ? kVariantV1MsgK : kVariantGeneral;
+  }
+  if (ctx->digits) return ctx->variant == kVariantV1 ? kVariantV1Digits : kVariantGeneralDigits;
+  if (ctx->variant != kVariantV1) return ctx->variant;
   if (nrows < thr) {
     // auto: one Euler step per byte only (with more, the exchanges outweigh the gain)
     const uint64_t split = ctx->launch.split_rows ? ctx->launch.split_rows

@@ -340,11 +340,15 @@ struct GeneralPath {
 // and alpha_j are the same coordinate and V_i = V_j is computed once; after
 // the (mu, Omega) lock that every part reaches within a few dozen bytes this
 // is one conversion per byte instead of three.
-template <uint32_t M, int MinCtas = LC_MIN_CTAS, uint32_t WM = (M ? (uint32_t)LC_WARM_MASK : 0u)>
+// kMsgK: each message may carry its own k in {3, 4}^3 (Eq. 7); bit i of
+// is3 marks k_i = 3 for this thread's message.
+template <uint32_t M, int MinCtas = LC_MIN_CTAS, uint32_t WM = (M ? (uint32_t)LC_WARM_MASK : 0u),
+          bool kMsgK = false>
 struct V1Path {
   double x, y, z, ax, ay, az;
   uint32_t V0, V1, V2;
   uint32_t mu0, mu1, mu2, om0, om1, om2;
+  uint32_t is3;
 
   static constexpr int kThetaRows = 4;
   static constexpr int kMinCtas = MinCtas;
@@ -381,7 +385,19 @@ struct V1Path {
     }
   }
   __device__ __forceinline__ static uint32_t rb(uint32_t V, uint32_t om) { return (V >> (8u * om)) & 255u; }
-  __device__ __forceinline__ void set_k(const DevMsg&, const DevParams&) {}  // k = (4, 4, 4)
+  __device__ __forceinline__ void set_k(const DevMsg& Mg, const DevParams&) {
+    // the context's k is (4, 4, 4); a message may carry its own
+    is3 = 0u;
+    if (kMsgK && (Mg.flags & kFlagMsgK)) {
+      for (uint32_t i = 0; i < 3; i++) is3 |= (((Mg.key_bits >> (20u + 4u * i)) & 15u) == 3u ? 1u : 0u) << i;
+    }
+  }
+  // v mod k_i for v < 2^16: v & 3 for k_i = 4; for k_i = 3, v - 3 floor(v / 3)
+  // with floor(v / 3) = (v * 43691) >> 17 (43691 = ceil(2^17 / 3))
+  __device__ __forceinline__ uint32_t modk(uint32_t v, uint32_t i) const {
+    if (!kMsgK) return v & 3u;
+    return ((is3 >> i) & 1u) ? v - 3u * ((v * 43691u) >> 17) : v & 3u;
+  }
 
   template <bool kDig = false>
   __device__ __forceinline__ uint32_t step(uint32_t in, uint32_t dec, const DevParams& p,
@@ -403,9 +419,9 @@ struct V1Path {
     mu1 = (mu1 + R2) % 3u;
     mu2 = (mu2 + R3) % 3u;
     set_alpha();
-    om0 = (om0 + rb(V0, om0)) & 3u;
-    om1 = (om1 + rb(V1, om1)) & 3u;
-    om2 = (om2 + rb(V2, om2)) & 3u;
+    om0 = modk(om0 + rb(V0, om0), 0u);
+    om1 = modk(om1 + rb(V1, om1), 1u);
+    om2 = modk(om2 + rb(V2, om2), 2u);
     x = f_add<(M & kEmuAprime) != 0>(x, ax);
     y = f_add<(M & kEmuAprime) != 0>(y, ay);
     z = f_add<(M & kEmuAprime) != 0>(z, az);
@@ -1012,6 +1028,8 @@ using KV1Lat = V1Path<0u>;
 using KV1Dense = V1Path<LC_EMU_MASK, 4>;
 using KV1Partial = V1Path<LC_PARTIAL_MASK, LC_MIN_CTAS, LC_PARTIAL_WARM_MASK>;
 using KV1PartialDense = V1Path<LC_PARTIAL_MASK, 4, LC_PARTIAL_WARM_MASK>;
+// the full-grid dense build for batches whose messages carry their own k
+using KV1MsgK = V1Path<LC_EMU_MASK, 4, LC_WARM_MASK, true>;
 
 }  // namespace
 
@@ -1041,6 +1059,7 @@ const void* batch_kernel_ptr(int variant) {
     case kVariantV1Dense: return reinterpret_cast<const void*>(&batch_kernel<KV1Dense>);
     case kVariantV1Partial: return reinterpret_cast<const void*>(&batch_kernel<KV1Partial>);
     case kVariantV1PartialDense: return reinterpret_cast<const void*>(&batch_kernel<KV1PartialDense>);
+    case kVariantV1MsgK: return reinterpret_cast<const void*>(&batch_kernel<KV1MsgK>);
     case kVariantV1Split: return reinterpret_cast<const void*>(&split_kernel);
     case kVariantV1Digits: return reinterpret_cast<const void*>(&batch_kernel<KV1, true>);
     case kVariantGeneralDigits: return reinterpret_cast<const void*>(&batch_kernel<KGeneral, true>);
@@ -1076,6 +1095,9 @@ cudaError_t launch_batch(int variant, int grid, int block, const uint8_t* ws, ui
       break;
     case kVariantV1PartialDense:
       batch_kernel<KV1PartialDense><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
+      break;
+    case kVariantV1MsgK:
+      batch_kernel<KV1MsgK><<<grid, block, smem, s>>>(ws, scratch, p, theta, dig, ct);
       break;
     case kVariantV1Split:
       if (block != kSplitThreads) return cudaErrorInvalidValue;

@@ -45,7 +45,9 @@ constexpr int kVariantV1PartialDense = 12;
 // The v1 constants, all binary64 work on the FP64 pipe, each part's three
 // coordinates on three warps of a 96-thread CTA (far-from-full batches).
 constexpr int kVariantV1Split = 13;
-constexpr int kNumVariants = 14;
+// kVariantV1Dense for batches whose messages carry their own k in {3, 4}^3.
+constexpr int kVariantV1MsgK = 14;
+constexpr int kNumVariants = 15;
 constexpr int kSplitThreads = 96;
 constexpr uint32_t kSplitRowsPerCta = 32;
 // Below this many parts per SM a v1 batch of the FP64-pipe variant runs split

@@ -771,10 +771,21 @@ KEYS = [
 
 @pytest.mark.parametrize("mode", [lc.LC_PARALLEL, lc.LC_SEQUENTIAL])
 @pytest.mark.parametrize("k_in_batch", [True, False], ids=["mixed-k", "lambda-only"])
-def test_per_request_lambda_and_k(ctx, mode, k_in_batch):
+@pytest.mark.parametrize("small", [0, 1], ids=["auto", "throughput-build"])
+def test_per_request_lambda_and_k(ctx, mode, k_in_batch, small):
     # One batch mixes requests with their own (lambda, k) and with the
     # context's; each equals the oracle run with those parameters, in both
-    # directions.  Without a k != 4 in the batch the v1 kernel variant runs.
+    # directions.  Without a k != 4 in the batch the v1 kernel variant runs;
+    # with one, a small batch runs the general path and, with the small-batch
+    # threshold at one part, the v1 build that reads k per message.
+    try:
+        assert lc.lc_ctx_set_launch(ctx.handle, 256, 0, 0, small) == lc.LC_OK
+        _per_request_lambda_and_k(ctx, mode, k_in_batch)
+    finally:
+        lc.lc_ctx_set_launch(ctx.handle, 256, 0)
+
+
+def _per_request_lambda_and_k(ctx, mode, k_in_batch):
     keys = KEYS if k_in_batch else [kk for kk in KEYS if kk[1] is None]
     items, expect, keep = [], [], []
     for i, n in enumerate([0, 1, 33, B, B + 1, 3 * B + 7, 20000, 70001]):
